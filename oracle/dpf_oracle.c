@@ -148,15 +148,20 @@ static void shift_rows(uint8_t state[4][4])
     memcpy(state, tmp, 16);
 }
 
+/* Sec. 4.2.1: multiplication by {02} is xtime(); {03} = {02} + {01}. */
+static uint8_t xtime(uint8_t a) { return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1b : 0x00)); }
+static uint8_t mul2(uint8_t a) { return xtime(a); }
+static uint8_t mul3(uint8_t a) { return (uint8_t)(xtime(a) ^ a); }
+
 static void mix_columns(uint8_t state[4][4])
 {
     /* Sec. 5.1.3 Eq. 5.6: multiplication by {03}x^3 + {01}x^2 + {01}x + {02}. */
     for (int c = 0; c < 4; c++) {
         uint8_t s0 = state[0][c], s1 = state[1][c], s2 = state[2][c], s3 = state[3][c];
-        state[0][c] = (uint8_t)(gf_mul(0x02, s0) ^ gf_mul(0x03, s1) ^ s2 ^ s3);
-        state[1][c] = (uint8_t)(s0 ^ gf_mul(0x02, s1) ^ gf_mul(0x03, s2) ^ s3);
-        state[2][c] = (uint8_t)(s0 ^ s1 ^ gf_mul(0x02, s2) ^ gf_mul(0x03, s3));
-        state[3][c] = (uint8_t)(gf_mul(0x03, s0) ^ s1 ^ s2 ^ gf_mul(0x02, s3));
+        state[0][c] = (uint8_t)(mul2(s0) ^ mul3(s1) ^ s2 ^ s3);
+        state[1][c] = (uint8_t)(s0 ^ mul2(s1) ^ mul3(s2) ^ s3);
+        state[2][c] = (uint8_t)(s0 ^ s1 ^ mul2(s2) ^ mul3(s3));
+        state[3][c] = (uint8_t)(mul3(s0) ^ s1 ^ s2 ^ mul2(s3));
     }
 }
 

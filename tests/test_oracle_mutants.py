@@ -28,8 +28,11 @@ MUTANTS = {
     # transposed operands: PRF keyed by the message instead of the node
     "prf_key_message_swapped": ("orc_aes128_encrypt(s, msg, out);", "orc_aes128_encrypt(msg, s, out);"),
     # wrong constant in MixColumns
-    "mixcolumns_coefficient": ("state[0][c] = (uint8_t)(gf_mul(0x02, s0) ^ gf_mul(0x03, s1) ^ s2 ^ s3);",
-                               "state[0][c] = (uint8_t)(gf_mul(0x02, s0) ^ gf_mul(0x02, s1) ^ s2 ^ s3);"),
+    "mixcolumns_coefficient": ("state[0][c] = (uint8_t)(mul2(s0) ^ mul3(s1) ^ s2 ^ s3);",
+                               "state[0][c] = (uint8_t)(mul2(s0) ^ mul2(s1) ^ s2 ^ s3);"),
+    # wrong reduction polynomial in xtime
+    "xtime_polynomial": ("return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1b : 0x00));",
+                         "return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1d : 0x00));"),
     # wrong round-constant progression
     "rcon_step": ("rcon = gf_mul(rcon, 0x02);", "rcon = gf_mul(rcon, 0x03);"),
     # output correction without the control-bit sign
