@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark of the DPF-PIR server hot path on GB300.
+
+One step = one pass of the whole server path over one batch of queries:
+key ingest from device memory, DPF full-domain expansion (AES-128 PRF) fused
+with the share x table product mod 2^32, and the reduction into the output
+shares (pir_server_eval_device).  The default workload is the batched one:
+a 2^20-row table of 64 u32 words (256 MiB, 2048-bit entries), 256 queries per
+step.  Inputs are seeded synthetic data (workloads/).
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank drives its own GPU
+with its own queries and table copy (queries are independent: weak scaling,
+no data-path collective); the process group only carries the barrier and the
+max-over-ranks timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "PIR queries/sec per server (bit-exact) and p50/p99 latency; plain vs batched/served"
+WORKLOADS = {
+    "batched_1m": dict(rows=1 << 20, width=64, batch=256, seed=20,
+                       desc="batched: 256 queries per step against one 2^20-row x 64-word u32 table "
+                            "(256 MiB, 2048-bit entries), AES-128 PRF, fused expand+contract"),
+    "plain_64k": dict(rows=1 << 16, width=16, batch=1, seed=16,
+                      desc="plain: one query per launch against a 2^16-row x 16-word u32 table (4 MiB)"),
+    "large_16m": dict(rows=1 << 24, width=32, batch=1024, seed=24,
+                      desc="large: 1024 queries per step against a 2^24-row x 32-word u32 table (2 GiB)"),
+}
+# Paper Table 4 (Sec. 5): 1M entries x 2048 bit, AES-128, one V100: 1,358 QPS (other hardware; context).
+PAPER_QPS = {"batched_1m": 1358.0}
+LOOKUPS_PER_NODE = 360  # table-lookup AES-128: 40 for the key expansion + 2 x 160 for the two blocks
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def dist_init(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank draws its own queries (weak scaling); rank 0 keeps the base seed."""
+    return base + 7919 * rank
+
+
+# ----------------------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.15)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swpc=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swpc", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gpu_id_for(device) -> str | None:
+    import torch
+
+    props = torch.cuda.get_device_properties(device)
+    bus = getattr(props, "pci_bus_id", None)
+    dom = getattr(props, "pci_domain_id", None)
+    dev = getattr(props, "pci_device_id", None)
+    if bus is None or dom is None or dev is None:
+        return None
+    return f"{dom:08X}:{bus:02X}:{dev:02X}.0"
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float = 20.0, max_wall_s: float = 60.0):
+    """Times the oracle (as it stands) on host threads: each thread evaluates whole
+    queries (FullEval + inner product).  Returns (qps, threads, queries, wall)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    oracle.build()
+    n = wl.domain_bits(rows)
+    threads = os.cpu_count() or 1
+    per_query_s = 1.7e-6 * (1 << n)  # the oracle's measured cost per tree node, roughly
+    queries = max(threads, min(int(target_cpu_s / per_query_s), 64 * threads))
+    queries = max(1, min(queries, int(max_wall_s / per_query_s) * threads))
+    rnd = wl.key_randomness(seed + 1, n, queries)
+    alphas = wl.alphas(seed + 1, rows, queries)
+    keys = [oracle.gen(n, int(a), 1, r0, r1, c0)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda k: oracle.answer(k, table_np), keys))
+    wall = time.perf_counter() - t0
+    return queries / wall, min(threads, queries), queries, wall
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def kernel_source_digest() -> str:
+    src = os.path.join(ROOT, "paper_2301_10904_gb300", "csrc", "dpf_eval.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_source_sha256_16") != kernel_source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+
+    import __graft_entry__ as g
+
+    rank, local_rank, world = dist_env()
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    dist_init(world, "nccl")
+    g.build()
+    import paper_2301_10904_gb300 as pir
+
+    wk = WORKLOADS[args.workload]
+    rows, width, batch = wk["rows"], wk["width"], wk["batch"]
+    seed = rank_seed(wk["seed"], rank)
+    n = pir.pir_domain_bits(rows)
+    kb = pir.pir_key_bytes(n)
+    stream = torch.cuda.current_stream(device)
+
+    table = wl.table_u32_torch(seed, rows, width, device)
+    alphas = wl.alphas(seed, rows, batch)
+    pairs = [pir.pir_keygen(n, int(a), 1, hashlib.sha256(b"bench%d-%d" % (seed, q)).digest())
+             for q, a in enumerate(alphas)]
+    keys0 = b"".join(p[0] for p in pairs)
+    keys1 = b"".join(p[1] for p in pairs)
+    dkeys = torch.frombuffer(bytearray(keys0), dtype=torch.uint8).to(device)
+    dout = torch.empty((batch, width), dtype=torch.int32, device=device)
+    plan = pir.pir_plan_for(rows, width, batch)
+
+    def step():
+        pir.pir_server_eval_device(table, dkeys, batch, dout, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    # steps: explicit, or enough for about three seconds of timed work
+    steps = args.steps
+    if steps is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        steps = int(min(2000, max(10, 3000.0 / max(e0.elapsed_time(e1), 1e-3))))
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(gpu_id_for(device) if rank == 0 else None)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    with sampler if rank == 0 else _Null():
+        for i in range(steps):
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize(device)
+        barrier(world, device)
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    total_ms = starts[0].elapsed_time(ends[-1])
+    total_ms = max_over_ranks(total_ms, world, device)
+    value = batch * world * steps / (total_ms / 1e3)
+
+    # correctness self-check outside the timed region: both servers reconstruct T[alpha]
+    dout1 = torch.empty_like(dout)
+    dkeys1 = torch.frombuffer(bytearray(keys1), dtype=torch.uint8).to(device)
+    pir.pir_server_eval_device(table, dkeys1, batch, dout1, stream=stream)
+    torch.cuda.synchronize(device)
+    rec = (dout.cpu().numpy().view(np.uint32).astype(np.uint64) + dout1.cpu().numpy().view(np.uint32)) & 0xFFFFFFFF
+    want = table[torch.from_numpy(alphas.astype(np.int64)).to(device)].cpu().numpy().view(np.uint32)
+    selfcheck = bool(np.array_equal(rec.astype(np.uint32), want))
+
+    # plain path on the same table: one query per launch
+    plain_lat = []
+    if batch > 1:
+        pk = [torch.frombuffer(bytearray(p[0]), dtype=torch.uint8).to(device) for p in pairs[:32]]
+        po = torch.empty((1, width), dtype=torch.int32, device=device)
+        for k in pk[:3]:
+            pir.pir_server_eval_device(table, k, 1, po, stream=stream)
+        torch.cuda.synchronize(device)
+        for k in pk:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pir.pir_server_eval_device(table, k, 1, po, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            plain_lat.append(a.elapsed_time(b))
+
+    # end to end through the public API: pinned host keys in, pinned host shares out
+    hkeys = torch.frombuffer(bytearray(keys0), dtype=torch.uint8).pin_memory()
+    hout = torch.empty((batch, width), dtype=torch.int32).pin_memory()
+    for _ in range(max(1, min(args.warmup, 3))):
+        pir.pir_server_eval(table, hkeys, batch, hout, stream=stream)
+    e2e_steps = max(3, min(steps, 50))
+    e2e_ms = []
+    barrier(world, device)
+    for _ in range(e2e_steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pir.pir_server_eval(table, hkeys, batch, hout, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = max_over_ranks(sum(e2e_ms), world, device)
+    e2e_ok = bool(np.array_equal(hout.numpy(), dout.cpu().numpy()))
+
+    if rank != 0:
+        return
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    clocks = sampler.summary()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    kernel_ms = statistics.mean(per_step)
+    nodes = batch * ((1 << n) - 1)  # internal tree nodes: one PRF evaluation (key schedule + 2 blocks) each
+    achieved = LOOKUPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e9
+    peak = sms * 32 * max_mhz * 1e6 / 1e9
+    traffic = profiled_traffic(args.workload)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": round(value / PAPER_QPS[args.workload], 3) if args.workload in PAPER_QPS else None,
+        "dtype": "u32",
+        "data": "synthetic (seeded SplitMix64 table, uniform alpha, keys from pir_keygen)",
+        "config": {"workload": wk["desc"], "rows": rows, "width_words": width, "batch": batch, "n": n,
+                   "prf": "AES-128", "l2": f"inputs larger than L2: table {rows * width * 4 >> 20} MiB per step, no flush",
+                   "plan": plan.as_dict(), "parallelism": f"{world} replica(s), independent queries"},
+        "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
+                       "p99": round(float(np.percentile(per_step, 99)), 4)},
+        "gpu_launches": steps,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Glookup/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "fused_eval_kernel", "kernel_ms": round(kernel_ms, 4),
+                     "work": f"{LOOKUPS_PER_NODE} AES table lookups x {nodes} tree nodes per launch",
+                     "peak_basis": f"{sms} SMs x 32 shared-memory lookups/clk x {max_mhz:.0f} MHz (derived)"},
+        "e2e": {"value": round(batch * world * e2e_steps / (e2e_total / 1e3), 2), "unit": "queries/s",
+                "h2d_bytes_per_step": batch * kb, "d2h_bytes_per_step": batch * width * 4,
+                "p50_ms": round(float(np.percentile(e2e_ms, 50)), 4), "bit_exact_vs_device": e2e_ok},
+        "selfcheck_reconstruct_all": selfcheck,
+        "clocks": clocks,
+    }
+    if plain_lat:
+        out["plain"] = {"qps": round(1e3 / statistics.mean(plain_lat), 2),
+                        "p50_ms": round(float(np.percentile(plain_lat, 50)), 4),
+                        "p99_ms": round(float(np.percentile(plain_lat, 99)), 4), "launches": len(plain_lat)}
+    if world == 1 and not args.no_cpu_baseline:
+        qps, cores, nq, wall = oracle_qps(rows, width, seed, table.cpu().numpy().view(np.uint32))
+        out["cpu_baseline"] = {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
+                                         f"{cores} host threads, {wall:.1f} s wall"}
+    print(json.dumps(out), flush=True)
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    wk = WORKLOADS[args.workload]
+    rows, width = wk["rows"], wk["width"]
+    table_np = wl.table_u32(wk["seed"], rows, width)
+    steps, warm = args.steps or 5, args.warmup
+    for _ in range(warm):
+        oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=2.0, max_wall_s=8.0)
+    times, queries, cores = [], 0, 1
+    for _ in range(steps):
+        qps, cores, nq, wall = oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=4.0, max_wall_s=12.0)
+        times.append(wall)
+        queries += nq
+    total = sum(times)
+    value = queries / total
+    out = {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 4), "unit": "queries/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": round(1e3 * total / steps, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wk["desc"], "rows": rows, "width_words": width},
+        "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{queries // steps} queries per step (oracle FullEval + inner product), "
+                                   f"{cores} host threads"},
+        "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * pir.h — C ABI of the GB300 DPF-PIR server library (libpir).
+ *
+ * Two-server private information retrieval over an embedding table T with L
+ * rows of W uint32 words, after Lam et al., "GPU-based Private Information
+ * Retrieval for On-Device Machine Learning Inference" (arXiv 2301.10904).
+ *
+ *   client: Gen(1^lambda, alpha) -> (k_0, k_1)            (Sec. 3.1, "DPF-PIR")
+ *   server sigma: share_sigma = T x Eval(k_sigma, {0..L-1})  (Sec. 3.1, Eqs. p1-p3)
+ *   client: T[alpha] * beta = share_0 + share_1 (mod 2^32)   (Sec. 3.1)
+ *
+ * All table, share and output arithmetic is integer mod 2^32; all tree
+ * arithmetic is 128-bit XOR with AES-128 as the PRF (Sec. 3.2.6).
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "device" pointers are CUDA device
+ *    memory of the current device; "host" pointers are ordinary or pinned
+ *    host memory.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream).
+ *  - The caller owns every buffer.  The library keeps no pointer after a
+ *    call returns.
+ *  - Return value: PIR_OK (0) or a negative PIR_ERR_* code.  No exceptions
+ *    cross the ABI.  Device-side key errors are reported through an
+ *    optional device status word (bit PIR_STATUS_BAD_KEY) because they are
+ *    only seen once the kernel runs.
+ *  - Calls that take device outputs are asynchronous on `stream`; calls that
+ *    write host outputs synchronize `stream` before returning.
+ *  - Domain: L >= 2 rows, n = ceil(log2 L) <= 40 tree levels; leaves j >= L
+ *    of the 2^n-leaf tree are evaluated but never multiplied.
+ *
+ * Key wire format (32 + 64 n bytes, little-endian, 16-byte aligned fields):
+ *   [0,4) "DPFK"  [4] version 1  [5] n  [6] party sigma (0/1)  [7] 0
+ *   [8,12) cw_out (u32)  [12,16) 0  [16,32) root seed P(0,0) of this party
+ *   [32 + 64(d-1) + 32t + 16b, +16) = codeword C_t[b][d], d = 1..n, t,b in {0,1}
+ * The 64 n codeword bytes are the paper's key size (Table 4: 896 B at 16K
+ * entries, 1280 B at 1M, 1408 B at 4M).
+ */
+#ifndef PIR_H
+#define PIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------- */
+#define PIR_OK 0
+#define PIR_ERR_ARG (-1)         /* null pointer, zero size, bad shape or stride */
+#define PIR_ERR_DOMAIN (-2)      /* key's n differs from ceil(log2 rows), alpha >= 2^n */
+#define PIR_ERR_KEY (-3)         /* malformed key header, unknown party */
+#define PIR_ERR_NOMEM (-4)       /* device or host allocation failed */
+#define PIR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define PIR_ERR_TIMEOUT (-6)     /* a bounded wait ran out */
+#define PIR_ERR_BUSY (-7)        /* admission refused (serving) */
+#define PIR_ERR_UNSUPPORTED (-8) /* shape outside the kernels' limits */
+
+#define PIR_STATUS_BAD_KEY 1u    /* device status bit: some key failed validation */
+
+#define PIR_KEY_HEADER_BYTES 32
+#define PIR_MAX_DOMAIN_BITS 40
+
+/* A table resident in device memory: row j of the table (j counted from the
+ * first row `data` points at) starts at data + j * stride.  data must be
+ * 4-byte aligned; 16-byte alignment with stride % 4 == 0 enables 128-bit
+ * loads. */
+typedef struct pir_table {
+    const uint32_t* data; /* device */
+    uint64_t rows;        /* L */
+    uint32_t width;       /* W, words per entry */
+    uint64_t stride;      /* words between consecutive rows, >= width */
+} pir_table;
+
+/* Launch shape of the fused kernel.  `group` queries share one CTA and one
+ * pass over each table tile; each CTA covers 2^range_log2 consecutive rows. */
+typedef struct pir_plan {
+    uint32_t group;      /* queries per CTA: 1, 2, 4 or 8 */
+    uint32_t range_log2; /* log2 rows per CTA, 1 <= range_log2 <= n */
+    uint32_t vec;        /* table words per load: 4 (128-bit) or 1 */
+    uint32_t ctas;       /* resulting grid size (output of pir_plan_for) */
+} pir_plan;
+
+/* ---- keys (host only) ----------------------------------------------- */
+
+/* Key size in bytes for an n-level tree: 32 + 64 n. */
+size_t pir_key_bytes(uint32_t n);
+
+/* Number of tree levels for a table of `rows` rows: ceil(log2 rows)
+ * (1 for rows <= 2).  Returns 0 for rows == 0 or rows > 2^40. */
+uint32_t pir_domain_bits(uint64_t rows);
+
+/* Gen(1^128, alpha) of Sec. 3.1, with the correction-word construction of
+ * BGI16 [dpf_1] (the paper defers key generation to it), in the codeword
+ * form C_t[b][d] of Eq. p3.  Writes pir_key_bytes(n) bytes to each of key0
+ * and key1 (host).  seed: 32 bytes of key material for a deterministic
+ * AES-128-CTR generator (tests, reproducible benchmarks), or NULL to draw
+ * from the operating system's entropy source.  Errors: PIR_ERR_ARG (null
+ * keys, n == 0 or n > 40), PIR_ERR_DOMAIN (alpha >= 2^n). */
+int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, uint8_t* key0, uint8_t* key1);
+
+/* Validates a key's header (magic, version, n, party, length == 32 + 64 n).
+ * On success stores n and the party (0 or 1).  Errors: PIR_ERR_ARG,
+ * PIR_ERR_KEY. */
+int pir_key_check(const uint8_t* key, size_t len, uint32_t* n, uint32_t* party);
+
+/* Client reconstruction (Sec. 3.1): out[i] = s0[i] + s1[i] mod 2^32 (host). */
+int pir_reconstruct(const uint32_t* s0, const uint32_t* s1, size_t w, uint32_t* out);
+
+/* ---- server evaluation ---------------------------------------------- */
+
+/* share_sigma[q] = sum_{j<L} Eval(k_q, j) * T[j]  (mod 2^32) for each of the
+ * `batch` keys (Sec. 3.1 "Eval"; fused with the table product as in
+ * Sec. 3.2.4, so the L-long share vector never reaches device memory).
+ * keys: host, batch * pir_key_bytes(n) bytes back to back, every key with
+ * n == pir_domain_bits(t->rows).  out: batch x width words, host or device
+ * (detected).  With a host `out` the call returns after the result is
+ * there.  Errors: PIR_ERR_ARG, PIR_ERR_KEY, PIR_ERR_DOMAIN, PIR_ERR_NOMEM,
+ * PIR_ERR_CUDA, PIR_ERR_UNSUPPORTED. */
+int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
+
+/* Same computation with keys and outputs already in device memory (the
+ * steady-state serving form).  dkeys: device, batch * pir_key_bytes(n)
+ * bytes, 16-byte aligned.  dout: device, batch x width words, overwritten.
+ * dstatus: optional device word; PIR_STATUS_BAD_KEY is OR-ed into it when a
+ * key fails validation on the device, and that query's share is 0.
+ * Asynchronous on `stream`. */
+int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
+                           uint32_t* dstatus, void* stream);
+
+/* As pir_server_eval_device with an explicit launch shape (autotuning,
+ * sweeps).  plan->ctas is ignored.  Errors: PIR_ERR_UNSUPPORTED for a shape
+ * the kernels cannot run. */
+int pir_server_eval_device_plan(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
+                                uint32_t* dstatus, const pir_plan* plan, void* stream);
+
+/* Index-range evaluation, the unit of multi-GPU sharding (Sec. 3.2.7: each
+ * GPU evaluates the DPF on a subset of indices and the partial results are
+ * summed, the final reduction being linear).  Computes
+ *   dout[q] = sum_{row_lo <= j < row_hi} Eval(k_q, j) * T[j]   (mod 2^32)
+ * where `shard` holds rows row_lo..row_hi-1 (shard->data points at row
+ * row_lo, shard->rows == row_hi - row_lo) and `domain_rows` is the full
+ * table's L, which fixes n.  Asynchronous; dout overwritten. */
+int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t domain_rows, const uint8_t* dkeys,
+                          size_t batch, uint32_t* dout, uint32_t* dstatus, void* stream);
+
+/* The launch shape the library picks for (rows, width, batch) on the current
+ * device (heuristic, or the autotuned entry when one is cached). */
+int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
+
+/* Human-readable name of an error code (static string). */
+const char* pir_error_string(int code);
+
+/* Text of the last CUDA error seen by this thread (static per thread). */
+const char* pir_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIR_H */

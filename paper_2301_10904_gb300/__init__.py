@@ -1,0 +1,196 @@
+"""GB300-native DPF-PIR server library: Python binding of libpir (include/pir.h).
+
+Every function below has the name of the C entry point it calls and does
+argument marshalling only; all computation happens in libpir's CUDA kernels
+(server side) or its C++ host code (client key generation and
+reconstruction).  There is no fallback: if the library is missing, import
+raises.
+
+Tables and device buffers are PyTorch CUDA tensors (torch.int32 holding u32
+bit patterns); host keys are `bytes`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libpir.so")
+
+PIR_OK = 0
+PIR_STATUS_BAD_KEY = 1
+ERRORS = {-1: "PIR_ERR_ARG", -2: "PIR_ERR_DOMAIN", -3: "PIR_ERR_KEY", -4: "PIR_ERR_NOMEM", -5: "PIR_ERR_CUDA",
+          -6: "PIR_ERR_TIMEOUT", -7: "PIR_ERR_BUSY", -8: "PIR_ERR_UNSUPPORTED"}
+
+
+class PirError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        detail = ""
+        if code == -5 or code == -4:
+            detail = f" [{_lib.pir_last_cuda_error().decode()}]"
+        super().__init__(f"{what}: {ERRORS.get(code, code)}{detail}")
+
+
+class pir_table(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("rows", ctypes.c_uint64), ("width", ctypes.c_uint32),
+                ("stride", ctypes.c_uint64)]
+
+
+class pir_plan(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32), ("vec", ctypes.c_uint32),
+                ("ctas", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libpir.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    u8p, u32p, vp = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    sig = {
+        "pir_key_bytes": (ctypes.c_size_t, [ctypes.c_uint32]),
+        "pir_domain_bits": (ctypes.c_uint32, [ctypes.c_uint64]),
+        "pir_keygen": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, u8p, u8p, u8p]),
+        "pir_key_check": (ctypes.c_int, [u8p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_uint32)]),
+        "pir_reconstruct": (ctypes.c_int, [u32p, u32p, ctypes.c_size_t, u32p]),
+        "pir_server_eval": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp]),
+        "pir_server_eval_device": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, u32p, vp]),
+        "pir_server_eval_device_plan": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, u32p,
+                                                       ctypes.POINTER(pir_plan), vp]),
+        "pir_server_eval_range": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_uint64, ctypes.c_uint64, u8p,
+                                                 ctypes.c_size_t, u32p, u32p, vp]),
+        "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
+        "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "pir_last_cuda_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+
+
+def _check(rc: int, what: str):
+    if rc != PIR_OK:
+        raise PirError(rc, what)
+
+
+def _buf(b: bytes):
+    return ctypes.cast(ctypes.c_char_p(b), ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def table_of(t, rows: int | None = None) -> pir_table:
+    """pir_table describing a 2-D CUDA tensor of 32-bit words."""
+    assert t.dim() == 2 and t.element_size() == 4 and t.is_cuda and t.stride(1) == 1
+    return pir_table(t.data_ptr(), t.shape[0] if rows is None else rows, t.shape[1], t.stride(0))
+
+
+# ------------------------------------------------------------------ keys (host)
+
+def pir_key_bytes(n: int) -> int:
+    return int(_lib.pir_key_bytes(n))
+
+
+def pir_domain_bits(rows: int) -> int:
+    return int(_lib.pir_domain_bits(rows))
+
+
+def pir_keygen(n: int, alpha: int, beta: int = 1, seed: bytes | None = None):
+    kb = pir_key_bytes(n)
+    k0 = ctypes.create_string_buffer(kb)
+    k1 = ctypes.create_string_buffer(kb)
+    if seed is not None and len(seed) != 32:
+        raise ValueError("seed must be 32 bytes")
+    sp = _buf(seed) if seed is not None else None
+    _check(_lib.pir_keygen(n, alpha, beta & 0xFFFFFFFF, sp, ctypes.cast(k0, ctypes.c_void_p),
+                           ctypes.cast(k1, ctypes.c_void_p)), "pir_keygen")
+    return k0.raw, k1.raw
+
+
+def pir_key_check(key: bytes):
+    n = ctypes.c_uint32()
+    party = ctypes.c_uint32()
+    _check(_lib.pir_key_check(_buf(key), len(key), ctypes.byref(n), ctypes.byref(party)), "pir_key_check")
+    return n.value, party.value
+
+
+def pir_reconstruct(s0, s1):
+    """(s0 + s1) mod 2^32 for host uint32 numpy arrays."""
+    import numpy as np
+
+    s0 = np.ascontiguousarray(s0, dtype=np.uint32)
+    s1 = np.ascontiguousarray(s1, dtype=np.uint32)
+    out = np.empty_like(s0)
+    _check(_lib.pir_reconstruct(s0.ctypes.data, s1.ctypes.data, s0.size, out.ctypes.data), "pir_reconstruct")
+    return out
+
+
+# ------------------------------------------------------------------ server
+
+def _host_ptr(x):
+    if isinstance(x, (bytes, bytearray)):
+        return _buf(bytes(x))
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def pir_server_eval(table, keys, batch: int, out, stream=None):
+    """Host keys (bytes, numpy or pinned CPU tensor holding batch * key_bytes
+    back to back) -> `out` (host numpy/CPU tensor or CUDA tensor) of
+    batch x width words."""
+    tb = table_of(table)
+    kbuf = bytes(keys) if isinstance(keys, (bytes, bytearray)) else keys
+    kptr = _buf(kbuf) if isinstance(kbuf, bytes) else _host_ptr(kbuf)
+    _check(_lib.pir_server_eval(ctypes.byref(tb), kptr, batch, _host_ptr(out), _stream(stream)), "pir_server_eval")
+    return out
+
+
+def pir_server_eval_device(table, dkeys, batch: int, dout, dstatus=None, stream=None):
+    tb = table_of(table)
+    _check(_lib.pir_server_eval_device(ctypes.byref(tb), dkeys.data_ptr(), batch, dout.data_ptr(),
+                                       dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
+           "pir_server_eval_device")
+    return dout
+
+
+def pir_server_eval_device_plan(table, dkeys, batch: int, dout, plan: pir_plan, dstatus=None, stream=None):
+    tb = table_of(table)
+    _check(_lib.pir_server_eval_device_plan(ctypes.byref(tb), dkeys.data_ptr(), batch, dout.data_ptr(),
+                                            dstatus.data_ptr() if dstatus is not None else None,
+                                            ctypes.byref(plan), _stream(stream)), "pir_server_eval_device_plan")
+    return dout
+
+
+def pir_server_eval_range(shard, row_lo: int, domain_rows: int, dkeys, batch: int, dout, dstatus=None, stream=None):
+    tb = table_of(shard)
+    _check(_lib.pir_server_eval_range(ctypes.byref(tb), row_lo, domain_rows, dkeys.data_ptr(), batch, dout.data_ptr(),
+                                      dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
+           "pir_server_eval_range")
+    return dout
+
+
+def pir_plan_for(rows: int, width: int, batch: int) -> pir_plan:
+    p = pir_plan()
+    _check(_lib.pir_plan_for(rows, width, batch, ctypes.byref(p)), "pir_plan_for")
+    return p
+
+
+def pir_error_string(code: int) -> str:
+    return _lib.pir_error_string(code).decode()

@@ -1,0 +1,169 @@
+// C-ABI server entry points: argument checks, buffer staging, dispatch.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace pir {
+
+static thread_local char g_cuda_msg[256] = "no CUDA error";
+
+int cuda_fail(int code, const char* what) {
+    std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s (%d)", what, cudaGetErrorString((cudaError_t)code), code);
+    return code == (int)cudaErrorMemoryAllocation ? PIR_ERR_NOMEM : PIR_ERR_CUDA;
+}
+
+#define CUDA_TRY(call, what)                                \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail((int)e_, what); \
+    } while (0)
+
+static bool table_ok(const pir_table* t) {
+    return t && t->data && t->rows >= 1 && t->width >= 1 && t->stride >= t->width &&
+           (reinterpret_cast<uintptr_t>(t->data) & 3u) == 0;
+}
+
+static bool vec_ok(const pir_table* t) {
+    return (reinterpret_cast<uintptr_t>(t->data) & 15u) == 0 && t->stride % 4 == 0 && t->width % 4 == 0;
+}
+
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // unregistered host memory on older runtimes
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Runs the fused evaluation of rows [row_lo, row_lo + shard->rows) of a
+// 2^n-leaf domain for device keys into a zeroed device output.
+static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
+                       uint32_t* dout, uint32_t* dstatus, const pir_plan* plan_in, void* stream) {
+    if (!table_ok(shard) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+    if (n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_DOMAIN;
+    if (row_lo + shard->rows > (1ull << n)) return PIR_ERR_DOMAIN;
+    const bool v = vec_ok(shard);
+    pir_plan plan{};
+    if (plan_in) {
+        plan = *plan_in;
+        int rc = plan_check(plan, n, shard->width, v);
+        if (rc != PIR_OK) return rc;
+    } else {
+        int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
+        if (rc != PIR_OK) return rc;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(dout, 0, batch * shard->width * sizeof(uint32_t), s), "memset shares");
+    EvalRequest req{};
+    req.table = shard->data;
+    req.row_lo = row_lo;
+    req.row_hi = row_lo + shard->rows;
+    req.width = shard->width;
+    req.stride = shard->stride;
+    req.n = n;
+    req.dkeys = dkeys;
+    req.batch = (uint32_t)batch;
+    req.dout = dout;
+    req.dstatus = dstatus;
+    return launch_fused(req, plan, stream);
+}
+
+}  // namespace pir
+
+extern "C" {
+
+const char* pir_error_string(int code) {
+    switch (code) {
+        case PIR_OK: return "ok";
+        case PIR_ERR_ARG: return "invalid argument";
+        case PIR_ERR_DOMAIN: return "key domain does not match the table";
+        case PIR_ERR_KEY: return "malformed key";
+        case PIR_ERR_NOMEM: return "out of memory";
+        case PIR_ERR_CUDA: return "CUDA error";
+        case PIR_ERR_TIMEOUT: return "timed out";
+        case PIR_ERR_BUSY: return "busy";
+        case PIR_ERR_UNSUPPORTED: return "unsupported shape";
+        default: return "unknown error";
+    }
+}
+
+const char* pir_last_cuda_error(void) { return pir::g_cuda_msg; }
+
+int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan) {
+    if (!plan || rows < 1 || width == 0 || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+    const uint32_t n = pir_domain_bits(rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    return pir::plan_fused(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, plan);
+}
+
+int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, uint32_t* dstatus,
+                           void* stream) {
+    if (!t) return PIR_ERR_ARG;
+    return pir::eval_device(t, 0, pir_domain_bits(t->rows), dkeys, batch, dout, dstatus, nullptr, stream);
+}
+
+int pir_server_eval_device_plan(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
+                                uint32_t* dstatus, const pir_plan* plan, void* stream) {
+    if (!t || !plan) return PIR_ERR_ARG;
+    return pir::eval_device(t, 0, pir_domain_bits(t->rows), dkeys, batch, dout, dstatus, plan, stream);
+}
+
+int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t domain_rows, const uint8_t* dkeys,
+                          size_t batch, uint32_t* dout, uint32_t* dstatus, void* stream) {
+    if (!shard || domain_rows < 1 || row_lo + shard->rows > domain_rows) return PIR_ERR_ARG;
+    return pir::eval_device(shard, row_lo, pir_domain_bits(domain_rows), dkeys, batch, dout, dstatus, nullptr, stream);
+}
+
+int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream) {
+    using namespace pir;
+    if (!table_ok(t) || !keys || !out || batch == 0) return PIR_ERR_ARG;
+    const uint32_t n = pir_domain_bits(t->rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    const size_t kb = key_bytes(n);
+    for (size_t q = 0; q < batch; ++q) {
+        uint32_t kn = 0, party = 0;
+        const uint8_t* k = keys + q * kb;
+        // the length is implied by the table's domain: check the header fields
+        int rc = pir_key_check(k, key_bytes(k[5] <= PIR_MAX_DOMAIN_BITS ? k[5] : 0), &kn, &party);
+        if (rc != PIR_OK) return PIR_ERR_KEY;
+        if (kn != n) return PIR_ERR_DOMAIN;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool out_on_device = is_device_pointer(out);
+    const size_t out_bytes = batch * (size_t)t->width * sizeof(uint32_t);
+    uint8_t* dkeys = nullptr;
+    uint32_t* dout = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&dkeys, batch * kb, s), "alloc keys");
+    int rc = PIR_OK;
+    if (!out_on_device) {
+        cudaError_t e = cudaMallocAsync((void**)&dout, out_bytes, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dkeys, s);
+            return cuda_fail((int)e, "alloc shares");
+        }
+    } else {
+        dout = out;
+    }
+    cudaError_t e = cudaMemcpyAsync(dkeys, keys, batch * kb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail((int)e, "copy keys");
+    if (rc == PIR_OK) rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, nullptr, stream);
+    if (rc == PIR_OK && !out_on_device) {
+        e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail((int)e, "copy shares");
+    }
+    if (!out_on_device) cudaFreeAsync(dout, s);
+    cudaFreeAsync(dkeys, s);
+    if (!out_on_device) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pir.h"
+
+namespace pir {
+
+// ---- host AES-128 (aes_host.cpp) -------------------------------------------
+// FIPS-197 AES-128 on 32-bit columns (byte r of column c at bits 8r of word c).
+struct Aes128 {
+    uint32_t rk[44];
+    void set_key(const uint8_t key[16]);
+    void encrypt(const uint8_t in[16], uint8_t out[16]) const;
+};
+const uint8_t* aes_sbox();  // the 256-byte S-box, derived once from GF(2^8)
+
+// ---- key layout -------------------------------------------------------------
+constexpr uint32_t kKeyMagic = 0x4B465044u;  // "DPFK" little-endian
+constexpr uint32_t kKeyVersion = 1;
+inline size_t key_bytes(uint32_t n) { return PIR_KEY_HEADER_BYTES + 64u * (size_t)n; }
+inline size_t codeword_offset(uint32_t d, uint32_t t, uint32_t b) {
+    return PIR_KEY_HEADER_BYTES + 64u * (size_t)(d - 1) + 32u * t + 16u * b;
+}
+
+// ---- device launch (dpf_eval.cu) --------------------------------------------
+struct EvalRequest {
+    const uint32_t* table;  // row `row_lo` of the evaluated rows
+    uint64_t row_lo, row_hi;
+    uint32_t width;
+    uint64_t stride;
+    uint32_t n;
+    const uint8_t* dkeys;
+    uint32_t batch;
+    uint32_t* dout;       // batch x width, accumulated into (zeroed by the caller)
+    uint32_t* dstatus;    // optional
+};
+
+int device_sm_count();
+int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
+               pir_plan* plan);
+int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
+int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream);
+
+// error bookkeeping (api.cpp)
+int cuda_fail(int cuda_error_code, const char* what);
+
+}  // namespace pir

@@ -1,0 +1,93 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py uses
+(the library's default plan through pir_server_eval_device).
+
+ - plain single query: 2^16 rows x 16 words, one key pair, both servers,
+   every output word against the oracle, then reconstruction;
+ - batched: 2^20 rows x 64 words, 256 queries: every query reconstructs
+   T[alpha] exactly (both servers on the GPU), and sampled queries match the
+   oracle's per-server share word for word;
+ - large table: 2^24 rows x 32 words (2 GiB), 1024 queries: same checks with
+   one sampled query per server (the oracle needs ~10 s per 2^24 expansion).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import oracle
+    import paper_2301_10904_gb300 as pir
+
+    return torch, pir, oracle
+
+
+def _keys(orc, n, alphas, seed):
+    ks0, ks1 = [], []
+    for (r0, r1, c0), a in zip(wl.key_randomness(seed, n, len(alphas)), alphas):
+        k0, k1 = orc.gen(n, int(a), 1, r0, r1, c0)
+        ks0.append(k0)
+        ks1.append(k1)
+    return ks0, ks1
+
+
+def _eval(torch, pir, table, keys, W):
+    dk = torch.frombuffer(bytearray(b"".join(keys)), dtype=torch.uint8).cuda()
+    out = torch.empty((len(keys), W), dtype=torch.int32, device="cuda")
+    pir.pir_server_eval_device(table, dk, len(keys), out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+def _oracle_sample(orc, keys, T, idx):
+    # oracle answers for a few queries, in parallel host threads (ctypes drops the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max(1, min(len(idx), os.cpu_count() or 1))) as ex:
+        return list(ex.map(lambda q: orc.answer(keys[q], T), idx))
+
+
+def _check_config(env, rows, width, batch, seed, sample):
+    torch, pir, orc = env
+    n = pir.pir_domain_bits(rows)
+    table = wl.table_u32_torch(seed, rows, width, "cuda")
+    alphas = wl.alphas(seed, rows, batch)
+    alphas[0] = rows - 1
+    alphas[-1] = 0
+    ks0, ks1 = _keys(orc, n, alphas, seed)
+    g0 = _eval(torch, pir, table, ks0, width)
+    g1 = _eval(torch, pir, table, ks1, width)
+    rec = (g0.astype(np.uint64) + g1) & 0xFFFFFFFF
+    rows_at = table[torch.from_numpy(alphas.astype(np.int64)).cuda()].cpu().numpy().view(np.uint32)
+    assert np.array_equal(rec.astype(np.uint32), rows_at)
+    T = table.cpu().numpy().view(np.uint32)
+    assert np.array_equal(T[[0, rows - 1]], wl.table_rows_u32(seed, width, [0, rows - 1]))
+    for q, want in zip(sample, _oracle_sample(orc, ks0, T, sample)):
+        assert np.array_equal(g0[q], want), q
+    q1 = sample[:1]
+    for q, want in zip(q1, _oracle_sample(orc, ks1, T, q1)):
+        assert np.array_equal(g1[q], want), q
+
+
+def test_plain_single_query_2p16x16(env):
+    _check_config(env, 1 << 16, 16, 1, 101, [0])
+
+
+def test_batched_2p20x64_b256(env):
+    _check_config(env, 1 << 20, 64, 256, 202, [0, 97, 255])
+
+
+def test_large_2p24x32_b1024(env):
+    _check_config(env, 1 << 24, 32, 1024, 404, [1023])

@@ -1,0 +1,226 @@
+"""Parity of the CUDA fused path with the oracle: bit-exact u32 shares.
+
+Keys come from the oracle's Gen with seeded randomness (workloads); tables
+from the seeded SplitMix64 generator.  Every share is compared element by
+element with the oracle's T x Eval(k, .) mod 2^32, and shares of the two
+servers must reconstruct beta * T[alpha] (Sec. 3.1).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+M32 = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import oracle
+    import paper_2301_10904_gb300 as pir
+
+    return torch, pir, oracle
+
+
+def make_keys(orc, n, alphas, betas, seed):
+    rnd = wl.key_randomness(seed, n, len(alphas))
+    ks0, ks1 = [], []
+    for (r0, r1, c0), a, b in zip(rnd, alphas, betas):
+        k0, k1 = orc.gen(n, int(a), int(b), r0, r1, c0)
+        ks0.append(k0)
+        ks1.append(k1)
+    return ks0, ks1
+
+
+def dev_table(torch, T):
+    return torch.from_numpy(np.ascontiguousarray(T).view(np.int32)).cuda()
+
+
+def dev_keys(torch, keys):
+    return torch.frombuffer(bytearray(b"".join(keys)), dtype=torch.uint8).cuda()
+
+
+def run_device(torch, pir, table, keys, W, plan=None, status=None):
+    dk = dev_keys(torch, keys)
+    out = torch.empty((len(keys), W), dtype=torch.int32, device="cuda")
+    if plan is None:
+        pir.pir_server_eval_device(table, dk, len(keys), out, status)
+    else:
+        pir.pir_server_eval_device_plan(table, dk, len(keys), out, plan, status)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+SHAPES = [  # (rows, width, batch): several tiles and ragged tails
+    (2, 1, 1), (3, 4, 2), (100, 3, 5), (1000, 16, 9), (4096 + 77, 16, 3), (1 << 14, 64, 8),
+    ((1 << 15) + 1000, 32, 11), (1 << 12, 1, 17), (1 << 13, 100, 4), (1 << 11, 256, 8),
+]
+
+
+@pytest.mark.parametrize("rows,width,batch", SHAPES)
+def test_fused_matches_oracle(env, rows, width, batch):
+    torch, pir, orc = env
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(rows * 7 + width, rows, width)
+    alphas = wl.alphas(rows, rows, batch)
+    alphas[0] = rows - 1
+    betas = [1] * batch
+    if batch > 1:
+        betas[1] = M32
+    ks0, ks1 = make_keys(orc, n, alphas, betas, rows + batch)
+    table = dev_table(torch, T)
+    g0 = run_device(torch, pir, table, ks0, width)
+    g1 = run_device(torch, pir, table, ks1, width)
+    for q in range(batch):
+        assert np.array_equal(g0[q], orc.answer(ks0[q], T)), q
+        assert np.array_equal(g1[q], orc.answer(ks1[q], T)), q
+        want = (T[alphas[q]].astype(np.uint64) * betas[q]) & M32
+        assert np.array_equal(pir.pir_reconstruct(g0[q], g1[q]), want.astype(np.uint32))
+
+
+def _plans(pir, n, width):
+    out = []
+    for g in (1, 2, 4, 8):
+        lsq = {1: 8, 2: 7, 4: 6, 8: 5}[g]
+        for vec in (1, 4):
+            if vec == 4 and width % 4:
+                continue
+            for r in sorted({1, 2, 3, min(n, lsq), min(n, lsq + 1), min(n, lsq + 3), min(n, lsq + 9)}):
+                if r < 1 or r > n or r - min(lsq, r - 1) > 9:
+                    continue
+                if g * width > 2048:
+                    continue
+                out.append(pir.pir_plan(g, r, vec, 0))
+    return out
+
+
+def test_every_launch_shape_matches_oracle(env):
+    torch, pir, orc = env
+    rows, width, batch = (1 << 13) + 333, 16, 9
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(21, rows, width)
+    alphas = wl.alphas(3, rows, batch)
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 77)
+    want = np.stack([orc.answer(k, T) for k in ks0])
+    table = dev_table(torch, T)
+    plans = _plans(pir, n, width)
+    assert len(plans) > 20
+    for plan in plans:
+        got = run_device(torch, pir, table, ks0, width, plan=plan)
+        assert np.array_equal(got, want), plan.as_dict()
+
+
+def test_host_entry_point_host_and_device_outputs(env):
+    torch, pir, orc = env
+    rows, width, batch = 5000, 8, 6
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(8, rows, width)
+    alphas = wl.alphas(8, rows, batch)
+    ks0, ks1 = make_keys(orc, n, alphas, [1] * batch, 8)
+    table = dev_table(torch, T)
+    host_out = np.zeros((batch, width), np.uint32)
+    pir.pir_server_eval(table, b"".join(ks0), batch, host_out)
+    dev_out = torch.zeros((batch, width), dtype=torch.int32, device="cuda")
+    pir.pir_server_eval(table, b"".join(ks1), batch, dev_out)
+    torch.cuda.synchronize()
+    d1 = dev_out.cpu().numpy().view(np.uint32)
+    for q in range(batch):
+        assert np.array_equal(host_out[q], orc.answer(ks0[q], T))
+        assert np.array_equal(d1[q], orc.answer(ks1[q], T))
+
+
+def test_host_entry_rejects_bad_keys_and_domains(env):
+    torch, pir, orc = env
+    T = wl.table_u32(1, 300, 4)
+    table = dev_table(torch, T)
+    k0, _ = make_keys(orc, 9, [5], [1], 1)
+    out = np.zeros((1, 4), np.uint32)
+    bad = bytearray(k0[0])
+    bad[0] ^= 1
+    with pytest.raises(pir.PirError) as e:
+        pir.pir_server_eval(table, bytes(bad), 1, out)
+    assert e.value.code == -3
+    k_wrong, _ = make_keys(orc, 10, [5], [1], 1)
+    with pytest.raises(pir.PirError) as e:
+        pir.pir_server_eval(table, k_wrong[0], 1, out)
+    assert e.value.code in (-2, -3)
+
+
+def test_device_status_flags_bad_key_and_zeroes_its_share(env):
+    torch, pir, orc = env
+    rows, width = 3000, 16
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(2, rows, width)
+    ks0, _ = make_keys(orc, n, [1, 2, 3, 4], [1] * 4, 2)
+    bad = bytearray(ks0[2])
+    bad[6] = 7  # party out of range
+    keys = [ks0[0], ks0[1], bytes(bad), ks0[3]]
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    got = run_device(torch, pir, dev_table(torch, T), keys, width, status=status)
+    assert int(status.item()) & pir.PIR_STATUS_BAD_KEY
+    assert not got[2].any()
+    for q in (0, 1, 3):
+        assert np.array_equal(got[q], orc.answer(ks0[q], T))
+
+
+def test_range_shards_sum_to_full_and_match_oracle(env):
+    # Sec. 3.2.7: shards over index ranges, summed, equal the full share.
+    torch, pir, orc = env
+    rows, width, batch = (1 << 14) + 100, 16, 5
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(4, rows, width)
+    alphas = wl.alphas(4, rows, batch)
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 4)
+    dk = dev_keys(torch, ks0)
+    table = dev_table(torch, T)
+    cuts = [0, 1, 4096, 4097, 10000, rows]
+    total = np.zeros((batch, width), np.uint64)
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        out = torch.empty((batch, width), dtype=torch.int32, device="cuda")
+        pir.pir_server_eval_range(table[lo:hi], lo, rows, dk, batch, out)
+        torch.cuda.synchronize()
+        part = out.cpu().numpy().view(np.uint32)
+        for q in range(batch):
+            assert np.array_equal(part[q], orc.answer(ks0[q], T, lo, hi)), (lo, hi, q)
+        total += part
+    total = (total & M32).astype(np.uint32)
+    for q in range(batch):
+        assert np.array_equal(total[q], orc.answer(ks0[q], T))
+
+
+def test_degenerate_domains_and_extreme_betas(env):
+    torch, pir, orc = env
+    for rows, width in ((2, 1), (2, 4), (3, 1), (5, 2)):
+        n = pir.pir_domain_bits(rows)
+        T = wl.table_u32(rows, rows, width)
+        table = dev_table(torch, T)
+        for alpha in (0, rows - 1):
+            for beta in (0, 1, M32):
+                ks0, ks1 = make_keys(orc, n, [alpha], [beta], alpha * 3 + rows)
+                g0 = run_device(torch, pir, table, ks0, width)
+                g1 = run_device(torch, pir, table, ks1, width)
+                assert np.array_equal(g0[0], orc.answer(ks0[0], T))
+                assert np.array_equal(g1[0], orc.answer(ks1[0], T))
+                want = (T[alpha].astype(np.uint64) * beta) & M32
+                assert np.array_equal(pir.pir_reconstruct(g0[0], g1[0]), want.astype(np.uint32))
+
+
+def test_library_keys_on_gpu_reconstruct(env):
+    torch, pir, _ = env
+    rows, width, batch = 1 << 12, 16, 8
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(6, rows, width)
+    alphas = wl.alphas(6, rows, batch)
+    pairs = [pir.pir_keygen(n, int(a), 1, None) for a in alphas]
+    table = dev_table(torch, T)
+    g0 = run_device(torch, pir, table, [p[0] for p in pairs], width)
+    g1 = run_device(torch, pir, table, [p[1] for p in pairs], width)
+    for q in range(batch):
+        assert np.array_equal(pir.pir_reconstruct(g0[q], g1[q]), T[alphas[q]])
