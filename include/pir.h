@@ -144,6 +144,27 @@ int pir_server_eval_device_plan(const pir_table* t, const uint8_t* dkeys, size_t
 int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t domain_rows, const uint8_t* dkeys,
                           size_t batch, uint32_t* dout, uint32_t* dstatus, void* stream);
 
+/* ---- materialised (unfused) baseline ------------------------------- */
+
+#define PIR_CONTRACT_IMAD 0  /* CUDA-core 32-bit multiply-add */
+
+/* Expansion only (the level-by-level strategy's output, Sec. 3.2.2): writes
+ * the full share vectors dshares[q * ld + j] = Eval(k_q, j) for j < rows,
+ * q < batch (device, u32; ld >= rows; 16-byte aligned with ld % 4 == 0
+ * enables vector stores).  O(batch x rows) device memory, which the fused
+ * path avoids (Sec. 3.2.4).  Keys as for pir_server_eval_device; a key that
+ * fails validation gets an all-zero share vector and sets PIR_STATUS_BAD_KEY
+ * in *dstatus.  Asynchronous. */
+int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, uint32_t* dshares, uint64_t ld,
+                           uint32_t* dstatus, void* stream);
+
+/* dout[q][w] = sum_{j < t->rows} dshares[q * ld + j] * T[j][w]  (mod 2^32),
+ * the share-matrix x table product of Sec. 3.1 ("batched together as a
+ * single matrix-matrix multiplication").  engine: PIR_CONTRACT_IMAD.
+ * dout (device, batch x width) is overwritten.  Asynchronous. */
+int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
+                     int engine, void* stream);
+
 /* The launch shape the library picks for (rows, width, batch) on the current
  * device (heuristic, or the autotuned entry when one is cached). */
 int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);

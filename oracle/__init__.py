@@ -185,6 +185,17 @@ def answer(key: bytes, table: np.ndarray, lo: int = 0, hi: int | None = None) ->
     return out
 
 
+def contract(S: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """Share matrix x table mod 2^32: out[b][w] = sum_k S[b][k] T[k][w]
+    (Sec. 3.1, the batched product).  numpy's integer matmul on uint64 is the
+    step: products of u32 fit in 64 bits and the wrap mod 2^64 preserves the
+    residue mod 2^32."""
+    S = np.ascontiguousarray(S, dtype=np.uint32).astype(np.uint64)
+    T = np.ascontiguousarray(T, dtype=np.uint32).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        return ((S @ T) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
 def reconstruct(s0: np.ndarray, s1: np.ndarray) -> np.ndarray:
     s0 = np.ascontiguousarray(s0, dtype=np.uint32)
     s1 = np.ascontiguousarray(s1, dtype=np.uint32)

@@ -63,6 +63,10 @@ def _load():
                                                        ctypes.POINTER(pir_plan), vp]),
         "pir_server_eval_range": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_uint64, ctypes.c_uint64, u8p,
                                                  ctypes.c_size_t, u32p, u32p, vp]),
+        "pir_expand_materialise": (ctypes.c_int, [ctypes.c_uint64, u8p, ctypes.c_size_t, u32p, ctypes.c_uint64, u32p,
+                                                  vp]),
+        "pir_contract_u32": (ctypes.c_int, [u32p, ctypes.c_uint64, ctypes.c_size_t, ctypes.POINTER(pir_table), u32p,
+                                            ctypes.c_int, vp]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
@@ -183,6 +187,25 @@ def pir_server_eval_range(shard, row_lo: int, domain_rows: int, dkeys, batch: in
     _check(_lib.pir_server_eval_range(ctypes.byref(tb), row_lo, domain_rows, dkeys.data_ptr(), batch, dout.data_ptr(),
                                       dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
            "pir_server_eval_range")
+    return dout
+
+
+PIR_CONTRACT_IMAD = 0
+
+
+def pir_expand_materialise(rows: int, dkeys, batch: int, dshares, dstatus=None, stream=None):
+    """Full share vectors into dshares (CUDA tensor [batch][ld], ld >= rows)."""
+    assert dshares.dim() == 2 and dshares.stride(1) == 1 and dshares.shape[1] >= rows
+    _check(_lib.pir_expand_materialise(rows, dkeys.data_ptr(), batch, dshares.data_ptr(), dshares.stride(0),
+                                       dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
+           "pir_expand_materialise")
+    return dshares
+
+
+def pir_contract_u32(dshares, batch: int, table, dout, engine: int = PIR_CONTRACT_IMAD, stream=None):
+    tb = table_of(table)
+    _check(_lib.pir_contract_u32(dshares.data_ptr(), dshares.stride(0), batch, ctypes.byref(tb), dout.data_ptr(),
+                                 engine, _stream(stream)), "pir_contract_u32")
     return dout
 
 

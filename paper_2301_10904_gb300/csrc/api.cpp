@@ -120,6 +120,38 @@ int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t doma
     return pir::eval_device(shard, row_lo, pir_domain_bits(domain_rows), dkeys, batch, dout, dstatus, nullptr, stream);
 }
 
+int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, uint32_t* dshares, uint64_t ld,
+                           uint32_t* dstatus, void* stream) {
+    using namespace pir;
+    if (!dkeys || !dshares || batch == 0 || batch > 0xffffffffu || rows < 1 || ld < rows) return PIR_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0 || (reinterpret_cast<uintptr_t>(dshares) & 3u) != 0)
+        return PIR_ERR_ARG;
+    const uint32_t n = pir_domain_bits(rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    pir_plan plan{};
+    int rc = plan_fused(rows, 0, n, 1, (uint32_t)batch, false, &plan);
+    if (rc != PIR_OK) return rc;
+    EvalRequest req{};
+    req.row_lo = 0;
+    req.row_hi = rows;
+    req.width = 1;
+    req.stride = 1;
+    req.n = n;
+    req.dkeys = dkeys;
+    req.batch = (uint32_t)batch;
+    req.dstatus = dstatus;
+    return launch_materialise(req, plan, dshares, ld, stream);
+}
+
+int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
+                     int engine, void* stream) {
+    using namespace pir;
+    if (!table_ok(t) || !dshares || !dout || batch == 0 || batch > 0xffffffffu || ld < t->rows) return PIR_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(dout, 0, batch * t->width * sizeof(uint32_t), s), "memset shares");
+    return launch_contract(dshares, ld, (uint32_t)batch, t->data, t->stride, t->width, t->rows, dout, engine, stream);
+}
+
 int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream) {
     using namespace pir;
     if (!table_ok(t) || !keys || !out || batch == 0) return PIR_ERR_ARG;

@@ -63,6 +63,10 @@ struct FusedParams {
     uint32_t n;
     uint32_t range_log2;
     uint32_t nqg;
+    // expand-only mode: shares[q * ld + (row - row_lo)] = y_q(row)
+    uint32_t* shares;
+    uint64_t ld;
+    uint32_t shares_vec;  // 1 when shares and ld allow 16-byte stores
 };
 
 // ---------------------------------------------------------------- GF(2^8)
@@ -231,8 +235,33 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
     }
 }
 
-template <int G, int VEC>
-__global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedParams p) {
+// Writes this thread's last 2*kc leaf shares (rows row_base .. row_base+2kc-1)
+// to the materialised share matrix.
+template <int G>
+__device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t* yb, uint32_t q, int g, int l,
+                                            uint64_t row_base, uint32_t kc) {
+    constexpr int SQ = kThreads / G;
+    uint32_t* dst = p.shares + (uint64_t)q * p.ld;
+    if (kc == 2 && p.shares_vec && row_base >= p.row_lo && row_base + 4 <= p.row_hi &&
+        ((row_base - p.row_lo) & 3u) == 0) {
+        uint4 v;
+        v.x = yb[(g * 2 * kPairs + 0) * SQ + l];
+        v.y = yb[(g * 2 * kPairs + 1) * SQ + l];
+        v.z = yb[(g * 2 * kPairs + 2) * SQ + l];
+        v.w = yb[(g * 2 * kPairs + 3) * SQ + l];
+        *reinterpret_cast<uint4*>(dst + (row_base - p.row_lo)) = v;
+        return;
+    }
+    for (uint32_t j = 0; j < 2 * kc; ++j) {
+        const uint64_t row = row_base + j;
+        if (row >= p.row_lo && row < p.row_hi) dst[row - p.row_lo] = yb[(g * 2 * kPairs + j) * SQ + l];
+    }
+}
+
+// The whole CTA program.  MAT = false: fused share x table product (a1-a6).
+// MAT = true: expansion only, leaf shares written to p.shares (a7 baseline).
+template <int G, int VEC, bool MAT>
+__device__ __forceinline__ void eval_body(const FusedParams& p) {
     constexpr int SQ = kThreads / G;
     constexpr int LOG_SQ = (SQ == 256) ? 8 : (SQ == 128) ? 7 : (SQ == 64) ? 6 : 5;
     static_assert(G * 2 * kPairs * SQ * 2 <= kYBufWords, "share buffers exceed their region");
@@ -340,8 +369,15 @@ __global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedPara
             yb[(g * 2 * kPairs + j + 1) * SQ + l] = y1;
             ++k;
             if (k % kc == 0) {
-                __syncthreads();
-                mac_phase<G, VEC>(p, yb, r0, m, sd, k - kc, kc, acc, tid);
+                if constexpr (MAT) {
+                    // each thread stores only what it wrote itself: no barrier needed
+                    const uint32_t q = qg * G + g;
+                    if (q < p.batch && l < nsub)
+                        store_phase<G>(p, yb, q, g, l, r0 + ((uint64_t)l << m) + 2ull * (k - kc), kc);
+                } else {
+                    __syncthreads();
+                    mac_phase<G, VEC>(p, yb, r0, m, sd, k - kc, kc, acc, tid);
+                }
                 ++phase;
             }
             if (k == npairs) break;
@@ -354,6 +390,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedPara
         }
     }
 
+    if constexpr (MAT) return;
     // ---- reduce the per-thread partial sums, then one atomic per word ------
     __syncthreads();
     const uint32_t W = p.width;
@@ -380,16 +417,27 @@ __global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedPara
 }
 
 template <int G, int VEC>
-cudaError_t launch_one(const FusedParams& p, uint32_t ctas, cudaStream_t s) {
-    auto kern = fused_eval_kernel<G, VEC>;
-    static bool configured = false;  // attribute is per device function; setting it again is harmless
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+__global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedParams p) {
+    eval_body<G, VEC, false>(p);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 3) expand_materialise_kernel(const FusedParams p) {
+    eval_body<G, 1, true>(p);
+}
+
+template <typename Kern>
+cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, cudaStream_t s) {
+    // the attribute is per function and device; setting it each launch costs ~1 us and is always correct
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
     kern<<<ctas, kThreads, kSmemBytes, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int G, int VEC>
+cudaError_t launch_one(const FusedParams& p, uint32_t ctas, cudaStream_t s) {
+    return launch_kernel(fused_eval_kernel<G, VEC>, p, ctas, s);
 }
 
 }  // namespace dev
@@ -446,8 +494,7 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     return PIR_OK;
 }
 
-int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
-    const uint32_t g = plan.group;
+static dev::FusedParams make_params(const EvalRequest& req, const pir_plan& plan) {
     dev::FusedParams p{};
     p.table = req.table;
     p.row_lo = req.row_lo;
@@ -462,7 +509,32 @@ int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
     p.batch = req.batch;
     p.n = req.n;
     p.range_log2 = plan.range_log2;
-    p.nqg = (req.batch + g - 1) / g;
+    p.nqg = (req.batch + plan.group - 1) / plan.group;
+    return p;
+}
+
+int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream) {
+    dev::FusedParams p = make_params(req, plan);
+    p.shares = shares;
+    p.ld = ld;
+    p.shares_vec = ((reinterpret_cast<uintptr_t>(shares) & 15u) == 0 && ld % 4 == 0) ? 1u : 0u;
+    const uint64_t ctas = ctas_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
+    if (ctas == 0) return PIR_OK;
+    if (ctas > 0x7fffffffull) return PIR_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    switch (plan.group) {
+        case 1: e = dev::launch_kernel(dev::expand_materialise_kernel<1>, p, (uint32_t)ctas, s); break;
+        case 2: e = dev::launch_kernel(dev::expand_materialise_kernel<2>, p, (uint32_t)ctas, s); break;
+        case 4: e = dev::launch_kernel(dev::expand_materialise_kernel<4>, p, (uint32_t)ctas, s); break;
+        default: e = dev::launch_kernel(dev::expand_materialise_kernel<8>, p, (uint32_t)ctas, s); break;
+    }
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "expand_materialise launch");
+}
+
+int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
+    const uint32_t g = plan.group;
+    dev::FusedParams p = make_params(req, plan);
     const uint64_t ctas = ctas_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
     if (ctas == 0) return PIR_OK;
     if (ctas > 0x7fffffffull) return PIR_ERR_UNSUPPORTED;

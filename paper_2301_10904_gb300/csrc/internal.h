@@ -43,6 +43,11 @@ int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t wi
                pir_plan* plan);
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream);
+int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream);
+
+// share matrix x table mod 2^32 (contract.cu); out is accumulated into
+int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                    uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream);
 
 // error bookkeeping (api.cpp)
 int cuda_fail(int cuda_error_code, const char* what);

@@ -1,0 +1,98 @@
+"""The materialised baseline (expansion to a share matrix in HBM, then the
+share-matrix x table product) against the oracle, and against the fused path."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from test_gpu_parity import dev_keys, dev_table, make_keys
+
+pytestmark = pytest.mark.gpu
+M32 = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    import oracle
+    import paper_2301_10904_gb300 as pir
+
+    return torch, pir, oracle
+
+
+@pytest.mark.parametrize("rows,batch,pad", [(2, 1, 0), (3, 2, 1), (1000, 9, 3), (4096, 8, 0), ((1 << 15) + 17, 5, 4),
+                                            (1 << 14, 17, 0)])
+def test_materialised_shares_match_oracle_full_eval(env, rows, batch, pad):
+    torch, pir, orc = env
+    n = pir.pir_domain_bits(rows)
+    alphas = wl.alphas(rows + 1, rows, batch)
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, rows + 2)
+    ld = rows + pad
+    S = torch.full((batch, ld), -1, dtype=torch.int32, device="cuda")
+    pir.pir_expand_materialise(rows, dev_keys(torch, ks0), batch, S)
+    torch.cuda.synchronize()
+    got = S.cpu().numpy().view(np.uint32)
+    for q in range(batch):
+        assert np.array_equal(got[q, :rows], orc.full_eval(ks0[q], rows)), q
+        assert (got[q, rows:] == M32).all()  # padding untouched
+
+
+def test_materialised_bad_key_gives_zero_vector_and_status(env):
+    torch, pir, orc = env
+    rows = 2000
+    n = pir.pir_domain_bits(rows)
+    ks0, _ = make_keys(orc, n, [3, 4], [1, 1], 5)
+    bad = bytearray(ks0[1])
+    bad[4] = 9  # version
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S = torch.full((2, rows), 7, dtype=torch.int32, device="cuda")
+    pir.pir_expand_materialise(rows, dev_keys(torch, [ks0[0], bytes(bad)]), 2, S, status)
+    torch.cuda.synchronize()
+    got = S.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got[0], orc.full_eval(ks0[0], rows))
+    assert not got[1].any() and int(status.item()) & 1
+
+
+@pytest.mark.parametrize("B,L,W", [(1, 1, 1), (3, 100, 5), (64, 4096, 64), (70, 3000, 65), (256, 1 << 14, 16),
+                                   (5, 777, 128)])
+def test_contract_matches_oracle(env, B, L, W):
+    torch, pir, orc = env
+    rng = np.random.Generator(np.random.PCG64(B * L + W))
+    S = rng.integers(0, 1 << 32, (B, L), dtype=np.uint64).astype(np.uint32)
+    T = wl.table_u32(W, L, W)
+    out = torch.empty((B, W), dtype=torch.int32, device="cuda")
+    pir.pir_contract_u32(torch.from_numpy(S.view(np.int32)).cuda(), B, dev_table(torch, T), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), orc.contract(S, T))
+
+
+def test_materialised_pipeline_equals_fused_and_oracle(env):
+    torch, pir, orc = env
+    rows, width, batch = (1 << 13) + 5, 32, 12
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(31, rows, width)
+    alphas = wl.alphas(31, rows, batch)
+    ks0, ks1 = make_keys(orc, n, alphas, [1] * batch, 31)
+    table = dev_table(torch, T)
+    outs = []
+    for keys in (ks0, ks1):
+        dk = dev_keys(torch, keys)
+        S = torch.empty((batch, rows), dtype=torch.int32, device="cuda")
+        pir.pir_expand_materialise(rows, dk, batch, S)
+        mat = torch.empty((batch, width), dtype=torch.int32, device="cuda")
+        pir.pir_contract_u32(S, batch, table, mat)
+        fused = torch.empty_like(mat)
+        pir.pir_server_eval_device(table, dk, batch, fused)
+        torch.cuda.synchronize()
+        m = mat.cpu().numpy().view(np.uint32)
+        assert np.array_equal(m, fused.cpu().numpy().view(np.uint32))
+        for q in (0, batch - 1):
+            assert np.array_equal(m[q], orc.answer(keys[q], T))
+        outs.append(m)
+    rec = (outs[0].astype(np.uint64) + outs[1]) & M32
+    assert np.array_equal(rec.astype(np.uint32), T[alphas])

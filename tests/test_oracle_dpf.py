@@ -182,3 +182,30 @@ def test_key_rejects_garbage(orc):
     bad[6] = 2
     with pytest.raises(ValueError):
         orc.full_eval(bytes(bad), 16)
+
+
+def test_contract_one_hot_selects_rows_and_agrees_with_answer(orc):
+    # closed form: a one-hot share matrix selects table rows (times beta)
+    L, W = 300, 9
+    T = wl.table_u32(12, L, W)
+    S = np.zeros((3, L), np.uint32)
+    S[0, 0] = 1
+    S[1, L - 1] = M32  # -1 mod 2^32
+    S[2, 7] = 3
+    out = orc.contract(S, T)
+    assert np.array_equal(out[0], T[0])
+    assert np.array_equal(out[1], ((-T[L - 1].astype(np.int64)) & M32).astype(np.uint32))
+    assert np.array_equal(out[2], ((T[7].astype(np.uint64) * 3) & M32).astype(np.uint32))
+    # the product with a full share vector is the server answer
+    k0, _ = _keys(orc, wl.domain_bits(L), 5, 1, 9)
+    assert np.array_equal(orc.contract(orc.full_eval(k0, L)[None, :], T)[0], orc.answer(k0, T))
+
+
+def test_contract_wraps_like_python_integers(orc):
+    rng = np.random.Generator(np.random.PCG64(3))
+    S = rng.integers(0, 1 << 32, (4, 50), dtype=np.uint64).astype(np.uint32)
+    T = rng.integers(0, 1 << 32, (50, 3), dtype=np.uint64).astype(np.uint32)
+    out = orc.contract(S, T)
+    for b in range(4):
+        for w in range(3):
+            assert int(out[b, w]) == sum(int(S[b, k]) * int(T[k, w]) for k in range(50)) % (1 << 32)
