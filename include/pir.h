@@ -144,6 +144,25 @@ int pir_server_eval_device_plan(const pir_table* t, const uint8_t* dkeys, size_t
 int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t domain_rows, const uint8_t* dkeys,
                           size_t batch, uint32_t* dout, uint32_t* dstatus, void* stream);
 
+/* Allocation-free form of pir_server_eval for callers that cannot let a
+ * library allocate device memory: a serving runtime that owns the whole
+ * device-memory budget, or a request path that must not take the
+ * allocator's locks or risk the device synchronisation an allocation can
+ * cause.  The paper has no counterpart; this is a deployment variant.
+ * Same inputs, output and result as pir_server_eval with host keys and a
+ * host `out` (batch x width words): keys and shares are staged through one
+ * fixed 256 KiB region of device memory that belongs to the library image
+ * (192 KiB for keys, 64 KiB for shares), so batch * pir_key_bytes(n) must
+ * be <= 196608 and batch * width * 4 <= 65536, else PIR_ERR_UNSUPPORTED.
+ * The call calls no device allocator and returns after `out` holds the
+ * shares.  The first call on a device looks up the region's device address
+ * (one-time set-up); make that first call before any stream capture.  All
+ * calls share the region, which keeps the last call's contents (the share
+ * area is cleared at the start of each call): calls that overlap on the GPU
+ * race, so issue them from one stream and one thread at a time.
+ * Errors: as pir_server_eval, plus PIR_ERR_UNSUPPORTED for the size limit. */
+int pir_server_eval_noalloc(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
+
 /* ---- materialised (unfused) baseline ------------------------------- */
 
 #define PIR_CONTRACT_IMAD 0  /* CUDA-core 32-bit multiply-add */

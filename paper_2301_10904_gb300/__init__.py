@@ -63,6 +63,7 @@ def _load():
                                                        ctypes.POINTER(pir_plan), vp]),
         "pir_server_eval_range": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_uint64, ctypes.c_uint64, u8p,
                                                  ctypes.c_size_t, u32p, u32p, vp]),
+        "pir_server_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp]),
         "pir_expand_materialise": (ctypes.c_int, [ctypes.c_uint64, u8p, ctypes.c_size_t, u32p, ctypes.c_uint64, u32p,
                                                   vp]),
         "pir_contract_u32": (ctypes.c_int, [u32p, ctypes.c_uint64, ctypes.c_size_t, ctypes.POINTER(pir_table), u32p,
@@ -163,6 +164,17 @@ def pir_server_eval(table, keys, batch: int, out, stream=None):
     kbuf = bytes(keys) if isinstance(keys, (bytes, bytearray)) else keys
     kptr = _buf(kbuf) if isinstance(kbuf, bytes) else _host_ptr(kbuf)
     _check(_lib.pir_server_eval(ctypes.byref(tb), kptr, batch, _host_ptr(out), _stream(stream)), "pir_server_eval")
+    return out
+
+
+def pir_server_eval_noalloc(table, keys, batch: int, out, stream=None):
+    """pir_server_eval through the library's fixed device staging region (no
+    device allocation); host keys in, host `out` (numpy/CPU tensor) out."""
+    tb = table_of(table)
+    kbuf = bytes(keys) if isinstance(keys, (bytes, bytearray)) else keys
+    kptr = _buf(kbuf) if isinstance(kbuf, bytes) else _host_ptr(kbuf)
+    _check(_lib.pir_server_eval_noalloc(ctypes.byref(tb), kptr, batch, _host_ptr(out), _stream(stream)),
+           "pir_server_eval_noalloc")
     return out
 
 
