@@ -320,6 +320,30 @@ def run_ours(args):
     e2e_total = max_over_ranks(sum(e2e_ms), world, device)
     e2e_ok = bool(np.array_equal(hout.numpy(), dout.cpu().numpy()))
 
+    # materialised baseline on the same inputs: share matrix in HBM, then S x T
+    materialised = None
+    if args.materialised and batch > 1:
+        S = torch.empty((batch, rows), dtype=torch.int32, device=device)
+        mout = torch.empty_like(dout)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        exp_ms, con_ms = [], []
+        for i in range(4):
+            ev[0].record(stream)
+            pir.pir_expand_materialise(rows, dkeys, batch, S, stream=stream)
+            ev[1].record(stream)
+            pir.pir_contract_u32(S, batch, table, mout, stream=stream)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            if i:
+                exp_ms.append(ev[0].elapsed_time(ev[1]))
+                con_ms.append(ev[1].elapsed_time(ev[2]))
+        tot = statistics.mean(exp_ms) + statistics.mean(con_ms)
+        materialised = {"qps": round(batch / (tot / 1e3), 2), "expand_ms": round(statistics.mean(exp_ms), 4),
+                        "contract_ms": round(statistics.mean(con_ms), 4),
+                        "share_matrix_bytes": batch * rows * 4,
+                        "bit_exact_vs_fused": bool(torch.equal(mout, dout))}
+        del S
+
     if rank != 0:
         return
     sms = torch.cuda.get_device_properties(device).multi_processor_count
@@ -360,6 +384,8 @@ def run_ours(args):
         "selfcheck_reconstruct_all": selfcheck,
         "clocks": clocks,
     }
+    if materialised:
+        out["materialised"] = materialised
     if plain_lat:
         out["plain"] = {"qps": round(1e3 / statistics.mean(plain_lat), 2),
                         "p50_ms": round(float(np.percentile(plain_lat, 50)), 4),
@@ -421,6 +447,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-materialised", dest="materialised", action="store_false",
+                    help="skip the materialised (share matrix in HBM) comparison leg")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
