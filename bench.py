@@ -45,6 +45,9 @@ WORKLOADS = {
                       desc="plain: one query per launch against a 2^16-row x 16-word u32 table (4 MiB)"),
     "large_16m": dict(rows=1 << 24, width=32, batch=1024, seed=24,
                       desc="large: 1024 queries per step against a 2^24-row x 32-word u32 table (2 GiB)"),
+    "multi_table": dict(seed=33, rows=None, width=None,
+                        desc="multi-table: 2048 queries Zipf(1.1) over 8 tables (2^16..2^22 rows, 16..128 words, "
+                             "1,460 MiB), one graph-captured persistent launch per step"),
 }
 # Paper Table 4 (Sec. 5): 1M entries x 2048 bit, AES-128, one V100: 1,358 QPS (other hardware; context).
 PAPER_QPS = {"batched_1m": 1358.0}
@@ -215,6 +218,232 @@ def profiled_traffic(workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def _pack_keys(keys, offsets, total):
+    buf = bytearray(total)
+    for k, o in zip(keys, offsets):
+        buf[int(o):int(o) + len(k)] = k
+    return buf
+
+
+class SingleTableWorkload:
+    """One table, one batch of queries per step (pir_server_eval_device)."""
+
+    def __init__(self, name, wk, pir, torch, device, stream, seed, args):
+        self.name, self.pir, self.torch, self.device, self.stream, self.args = name, pir, torch, device, stream, args
+        self.rows, self.width, self.batch = wk["rows"], wk["width"], wk["batch"]
+        self.desc = wk["desc"]
+        self.n = pir.pir_domain_bits(self.rows)
+        self.kb = pir.pir_key_bytes(self.n)
+        self.seed = seed
+        self.table = wl.table_u32_torch(seed, self.rows, self.width, device)
+        self.alphas = wl.alphas(seed, self.rows, self.batch)
+        self.pairs = [pir.pir_keygen(self.n, int(a), 1, hashlib.sha256(b"bench%d-%d" % (seed, q)).digest())
+                      for q, a in enumerate(self.alphas)]
+        self.keys0 = b"".join(p[0] for p in self.pairs)
+        self.keys1 = b"".join(p[1] for p in self.pairs)
+        self.dkeys = torch.frombuffer(bytearray(self.keys0), dtype=torch.uint8).to(device)
+        self.dout = torch.empty((self.batch, self.width), dtype=torch.int32, device=device)
+        self.plan = pir.pir_plan_for(self.rows, self.width, self.batch)
+        self.queries_per_step = self.batch
+        self.nodes_per_step = self.batch * ((1 << self.n) - 1)
+        self.kernel = "fused_eval_kernel"
+        self.h2d_bytes, self.d2h_bytes = self.batch * self.kb, self.batch * self.width * 4
+        self.hkeys = torch.frombuffer(bytearray(self.keys0), dtype=torch.uint8).pin_memory()
+        self.hout = torch.empty((self.batch, self.width), dtype=torch.int32).pin_memory()
+
+    def step(self):
+        self.pir.pir_server_eval_device(self.table, self.dkeys, self.batch, self.dout, stream=self.stream)
+
+    def e2e_step(self):
+        self.pir.pir_server_eval(self.table, self.hkeys, self.batch, self.hout, stream=self.stream)
+
+    def e2e_matches(self):
+        return bool(np.array_equal(self.hout.numpy(), self.dout.cpu().numpy()))
+
+    def selfcheck(self):
+        torch, pir = self.torch, self.pir
+        d1 = torch.empty_like(self.dout)
+        k1 = torch.frombuffer(bytearray(self.keys1), dtype=torch.uint8).to(self.device)
+        pir.pir_server_eval_device(self.table, k1, self.batch, d1, stream=self.stream)
+        torch.cuda.synchronize(self.device)
+        rec = (self.dout.cpu().numpy().view(np.uint32).astype(np.uint64) + d1.cpu().numpy().view(np.uint32))
+        want = self.table[torch.from_numpy(self.alphas.astype(np.int64)).to(self.device)].cpu().numpy()
+        return bool(np.array_equal((rec & 0xFFFFFFFF).astype(np.uint32), want.view(np.uint32)))
+
+    def config(self):
+        return {"workload": self.desc, "rows": self.rows, "width_words": self.width, "batch": self.batch,
+                "n": self.n, "prf": "AES-128",
+                "l2": f"inputs larger than L2: table {self.rows * self.width * 4 >> 20} MiB per step, no flush"
+                if self.rows * self.width * 4 > 129e6 else "table fits in L2; no flush (resident-table serving)",
+                "plan": self.plan.as_dict()}
+
+    def extras(self):
+        torch, pir, stream = self.torch, self.pir, self.stream
+        out = {}
+        if self.batch > 1:  # plain path on the same table: one query per launch
+            pk = [torch.frombuffer(bytearray(p[0]), dtype=torch.uint8).to(self.device) for p in self.pairs[:32]]
+            po = torch.empty((1, self.width), dtype=torch.int32, device=self.device)
+            for k in pk[:3]:
+                pir.pir_server_eval_device(self.table, k, 1, po, stream=stream)
+            torch.cuda.synchronize(self.device)
+            lat = []
+            for k in pk:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pir.pir_server_eval_device(self.table, k, 1, po, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                lat.append(a.elapsed_time(b))
+            out["plain"] = {"qps": round(1e3 / statistics.mean(lat), 2),
+                            "p50_ms": round(float(np.percentile(lat, 50)), 4),
+                            "p99_ms": round(float(np.percentile(lat, 99)), 4), "launches": len(lat)}
+        if self.args.materialised and self.batch > 1 and self.batch * self.rows * 4 <= (8 << 30):
+            S = torch.empty((self.batch, self.rows), dtype=torch.int32, device=self.device)
+            mout = torch.empty_like(self.dout)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            exp_ms, con_ms = [], []
+            for i in range(4):
+                ev[0].record(stream)
+                pir.pir_expand_materialise(self.rows, self.dkeys, self.batch, S, stream=stream)
+                ev[1].record(stream)
+                pir.pir_contract_u32(S, self.batch, self.table, mout, stream=stream)
+                ev[2].record(stream)
+                ev[2].synchronize()
+                if i:
+                    exp_ms.append(ev[0].elapsed_time(ev[1]))
+                    con_ms.append(ev[1].elapsed_time(ev[2]))
+            tot = statistics.mean(exp_ms) + statistics.mean(con_ms)
+            out["materialised"] = {"qps": round(self.batch / (tot / 1e3), 2),
+                                   "expand_ms": round(statistics.mean(exp_ms), 4),
+                                   "contract_ms": round(statistics.mean(con_ms), 4),
+                                   "share_matrix_bytes": self.batch * self.rows * 4,
+                                   "bit_exact_vs_fused": bool(torch.equal(mout, self.dout))}
+            del S
+        return out
+
+    def cpu_baseline(self):
+        qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, self.table.cpu().numpy().view(np.uint32))
+        return {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
+                          f"{cores} host threads, {wall:.1f} s wall"}
+
+
+class MultiTableWorkload:
+    """Eight tables of uneven sizes and widths, 2048 queries Zipf(1.1) over them,
+    one graph-captured persistent launch per step; item size from the autotuner."""
+
+    def __init__(self, name, wk, pir, torch, device, stream, seed, args):
+        self.name, self.pir, self.torch, self.device, self.stream, self.args = name, pir, torch, device, stream, args
+        self.desc = wk["desc"]
+        self.shapes = list(zip(wl.MULTI_TABLE_ROWS, wl.MULTI_TABLE_WIDTHS))
+        self.batch = wl.MULTI_TABLE_QUERIES
+        self.seed = seed
+        self.assign = wl.zipf_assignment(seed, len(self.shapes), self.batch)
+        self.tables = [wl.table_u32_torch(seed * 100 + i, r, w, device) for i, (r, w) in enumerate(self.shapes)]
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.alphas = [int(rng.integers(0, self.shapes[t][0])) for t in self.assign]
+        self.ns = [pir.pir_domain_bits(r) for r, _ in self.shapes]
+        self.pairs = [pir.pir_keygen(self.ns[t], a, 1, hashlib.sha256(b"multi%d-%d" % (seed, q)).digest())
+                      for q, (t, a) in enumerate(zip(self.assign, self.alphas))]
+        probe = pir.pir_multi_plan_create(self.tables, self.assign)
+        self.keys0 = _pack_keys([p[0] for p in self.pairs], probe.key_offsets, probe.key_bytes_total)
+        self.keys1 = _pack_keys([p[1] for p in self.pairs], probe.key_offsets, probe.key_bytes_total)
+        self.dkeys = torch.frombuffer(bytearray(self.keys0), dtype=torch.uint8).to(device)
+        self.dout = torch.empty((probe.out_words_total,), dtype=torch.int32, device=device)
+        self.item_log2, self.tune_ms = pir.pir_multi_autotune(self.tables, self.assign, self.dkeys, self.dout,
+                                                              stream=stream)
+        probe.close()
+        self.plan = pir.pir_multi_plan_create(self.tables, self.assign, self.item_log2)
+        self.graph = pir.pir_multi_graph_create(self.plan, self.dkeys, self.dout)
+        self.queries_per_step = self.batch
+        self.nodes_per_step = sum((1 << self.ns[t]) - 1 for t in self.assign)
+        self.kernel = "multi_eval_kernel"
+        self.h2d_bytes, self.d2h_bytes = self.plan.key_bytes_total, self.plan.out_words_total * 4
+        self.hkeys = torch.frombuffer(bytearray(self.keys0), dtype=torch.uint8).pin_memory()
+        self.hout = torch.empty((self.plan.out_words_total,), dtype=torch.int32).pin_memory()
+
+    def step(self):
+        self.graph.launch(self.stream)
+
+    def e2e_step(self):
+        self.pir.pir_server_eval_multi_host(self.plan, self.hkeys, self.hout, stream=self.stream)
+
+    def e2e_matches(self):
+        return bool(np.array_equal(self.hout.numpy(), self.dout.cpu().numpy()))
+
+    def selfcheck(self):
+        torch, pir = self.torch, self.pir
+        d1 = torch.empty_like(self.dout)
+        k1 = torch.frombuffer(bytearray(self.keys1), dtype=torch.uint8).to(self.device)
+        pir.pir_server_eval_multi(self.plan, k1, d1, stream=self.stream)
+        torch.cuda.synchronize(self.device)
+        a, b = self.dout.cpu().numpy().view(np.uint32), d1.cpu().numpy().view(np.uint32)
+        for q, t in enumerate(self.assign):
+            o, w = int(self.plan.out_offsets[q]), self.shapes[t][1]
+            rec = ((a[o:o + w].astype(np.uint64) + b[o:o + w]) & 0xFFFFFFFF).astype(np.uint32)
+            if not np.array_equal(rec, self.tables[t][self.alphas[q]].cpu().numpy().view(np.uint32)):
+                return False
+        return True
+
+    def config(self):
+        counts = np.bincount(self.assign, minlength=len(self.shapes)).tolist()
+        return {"workload": self.desc, "tables": [{"rows": r, "width_words": w} for r, w in self.shapes],
+                "queries": self.batch, "queries_per_table": counts, "prf": "AES-128",
+                "tables_mib": round(sum(r * w * 4 for r, w in self.shapes) / 2**20, 1),
+                "l2": "inputs larger than L2 (1,460 MiB of tables per step), no flush",
+                "plan": {"item_log2": self.item_log2, "items": self.plan.items, "autotune_ms": round(self.tune_ms, 3),
+                         "graph": True}}
+
+    def extras(self):
+        # one launch per table (pir_server_eval_device on each table's queries), back to back
+        torch, pir, stream = self.torch, self.pir, self.stream
+        per = []
+        for t in range(len(self.shapes)):
+            qs = [q for q, tt in enumerate(self.assign) if tt == t]
+            if not qs:
+                continue
+            kb = pir.pir_key_bytes(self.ns[t])
+            keys = torch.frombuffer(bytearray(b"".join(self.pairs[q][0] for q in qs)), dtype=torch.uint8).to(self.device)
+            per.append((t, len(qs), keys, torch.empty((len(qs), self.shapes[t][1]), dtype=torch.int32,
+                                                      device=self.device)))
+            del kb
+        def run():
+            for t, nq, keys, out in per:
+                pir.pir_server_eval_device(self.tables[t], keys, nq, out, stream=stream)
+        run()
+        torch.cuda.synchronize(self.device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            run()
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / 3
+        return {"per_table_launches": {"qps": round(self.batch / (ms / 1e3), 2), "ms": round(ms, 4),
+                                       "launches": len(per)}}
+
+    def cpu_baseline(self):
+        from concurrent.futures import ThreadPoolExecutor
+
+        import oracle
+
+        oracle.build()
+        threads = os.cpu_count() or 1
+        sample = list(range(0, self.batch, max(1, self.batch // (2 * threads))))[: 2 * threads]
+        host = [t.cpu().numpy().view(np.uint32) for t in self.tables]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda q: oracle.answer(self.pairs[q][0], host[self.assign[q]]), sample))
+        wall = time.perf_counter() - t0
+        return {"value": round(len(sample) / wall, 4), "unit": "queries/s", "cores": min(threads, len(sample)),
+                "kind": "oracle", "sample": f"{len(sample)} queries spread over the Zipf mix (oracle FullEval + "
+                                            f"inner product), {min(threads, len(sample))} host threads, {wall:.1f} s wall"}
+
+
+WORKLOAD_CLASSES = {"batched_1m": SingleTableWorkload, "plain_64k": SingleTableWorkload,
+                    "large_16m": SingleTableWorkload, "multi_table": MultiTableWorkload}
+
+
 def run_ours(args):
     import torch
 
@@ -228,34 +457,18 @@ def run_ours(args):
     import paper_2301_10904_gb300 as pir
 
     wk = WORKLOADS[args.workload]
-    rows, width, batch = wk["rows"], wk["width"], wk["batch"]
-    seed = rank_seed(wk["seed"], rank)
-    n = pir.pir_domain_bits(rows)
-    kb = pir.pir_key_bytes(n)
     stream = torch.cuda.current_stream(device)
-
-    table = wl.table_u32_torch(seed, rows, width, device)
-    alphas = wl.alphas(seed, rows, batch)
-    pairs = [pir.pir_keygen(n, int(a), 1, hashlib.sha256(b"bench%d-%d" % (seed, q)).digest())
-             for q, a in enumerate(alphas)]
-    keys0 = b"".join(p[0] for p in pairs)
-    keys1 = b"".join(p[1] for p in pairs)
-    dkeys = torch.frombuffer(bytearray(keys0), dtype=torch.uint8).to(device)
-    dout = torch.empty((batch, width), dtype=torch.int32, device=device)
-    plan = pir.pir_plan_for(rows, width, batch)
-
-    def step():
-        pir.pir_server_eval_device(table, dkeys, batch, dout, stream=stream)
+    W = WORKLOAD_CLASSES[args.workload](args.workload, wk, pir, torch, device, stream,
+                                        rank_seed(wk["seed"], rank), args)
 
     for _ in range(args.warmup):
-        step()
+        W.step()
     torch.cuda.synchronize(device)
-    # steps: explicit, or enough for about three seconds of timed work
-    steps = args.steps
+    steps = args.steps  # explicit, or enough for about three seconds of timed work
     if steps is None:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        W.step()
         e1.record(stream)
         torch.cuda.synchronize(device)
         steps = int(min(2000, max(10, 3000.0 / max(e0.elapsed_time(e1), 1e-3))))
@@ -268,81 +481,32 @@ def run_ours(args):
     with sampler if rank == 0 else _Null():
         for i in range(steps):
             starts[i].record(stream)
-            step()
+            W.step()
             ends[i].record(stream)
         torch.cuda.synchronize(device)
         barrier(world, device)
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = starts[0].elapsed_time(ends[-1])
-    total_ms = max_over_ranks(total_ms, world, device)
-    value = batch * world * steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(starts[0].elapsed_time(ends[-1]), world, device)
+    value = W.queries_per_step * world * steps / (total_ms / 1e3)
 
-    # correctness self-check outside the timed region: both servers reconstruct T[alpha]
-    dout1 = torch.empty_like(dout)
-    dkeys1 = torch.frombuffer(bytearray(keys1), dtype=torch.uint8).to(device)
-    pir.pir_server_eval_device(table, dkeys1, batch, dout1, stream=stream)
-    torch.cuda.synchronize(device)
-    rec = (dout.cpu().numpy().view(np.uint32).astype(np.uint64) + dout1.cpu().numpy().view(np.uint32)) & 0xFFFFFFFF
-    want = table[torch.from_numpy(alphas.astype(np.int64)).to(device)].cpu().numpy().view(np.uint32)
-    selfcheck = bool(np.array_equal(rec.astype(np.uint32), want))
-
-    # plain path on the same table: one query per launch
-    plain_lat = []
-    if batch > 1:
-        pk = [torch.frombuffer(bytearray(p[0]), dtype=torch.uint8).to(device) for p in pairs[:32]]
-        po = torch.empty((1, width), dtype=torch.int32, device=device)
-        for k in pk[:3]:
-            pir.pir_server_eval_device(table, k, 1, po, stream=stream)
-        torch.cuda.synchronize(device)
-        for k in pk:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pir.pir_server_eval_device(table, k, 1, po, stream=stream)
-            b.record(stream)
-            b.synchronize()
-            plain_lat.append(a.elapsed_time(b))
+    selfcheck = W.selfcheck()  # outside the timed region: both servers reconstruct T[alpha]
 
     # end to end through the public API: pinned host keys in, pinned host shares out
-    hkeys = torch.frombuffer(bytearray(keys0), dtype=torch.uint8).pin_memory()
-    hout = torch.empty((batch, width), dtype=torch.int32).pin_memory()
     for _ in range(max(1, min(args.warmup, 3))):
-        pir.pir_server_eval(table, hkeys, batch, hout, stream=stream)
+        W.e2e_step()
     e2e_steps = max(3, min(steps, 50))
     e2e_ms = []
     barrier(world, device)
     for _ in range(e2e_steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pir.pir_server_eval(table, hkeys, batch, hout, stream=stream)
+        W.e2e_step()
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_total = max_over_ranks(sum(e2e_ms), world, device)
-    e2e_ok = bool(np.array_equal(hout.numpy(), dout.cpu().numpy()))
-
-    # materialised baseline on the same inputs: share matrix in HBM, then S x T
-    materialised = None
-    if args.materialised and batch > 1:
-        S = torch.empty((batch, rows), dtype=torch.int32, device=device)
-        mout = torch.empty_like(dout)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        exp_ms, con_ms = [], []
-        for i in range(4):
-            ev[0].record(stream)
-            pir.pir_expand_materialise(rows, dkeys, batch, S, stream=stream)
-            ev[1].record(stream)
-            pir.pir_contract_u32(S, batch, table, mout, stream=stream)
-            ev[2].record(stream)
-            ev[2].synchronize()
-            if i:
-                exp_ms.append(ev[0].elapsed_time(ev[1]))
-                con_ms.append(ev[1].elapsed_time(ev[2]))
-        tot = statistics.mean(exp_ms) + statistics.mean(con_ms)
-        materialised = {"qps": round(batch / (tot / 1e3), 2), "expand_ms": round(statistics.mean(exp_ms), 4),
-                        "contract_ms": round(statistics.mean(con_ms), 4),
-                        "share_matrix_bytes": batch * rows * 4,
-                        "bit_exact_vs_fused": bool(torch.equal(mout, dout))}
-        del S
+    e2e_ok = W.e2e_matches()
+    extras = W.extras()
 
     if rank != 0:
         return
@@ -350,10 +514,10 @@ def run_ours(args):
     clocks = sampler.summary()
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     kernel_ms = statistics.mean(per_step)
-    nodes = batch * ((1 << n) - 1)  # internal tree nodes: one PRF evaluation (key schedule + 2 blocks) each
-    achieved = LOOKUPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e9
+    achieved = LOOKUPS_PER_NODE * W.nodes_per_step / (kernel_ms / 1e3) / 1e9
     peak = sms * 32 * max_mhz * 1e6 / 1e9
-    traffic = profiled_traffic(args.workload)
+    cfg = W.config()
+    cfg["parallelism"] = f"{world} replica(s), independent queries"
     out = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -366,35 +530,25 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": round(value / PAPER_QPS[args.workload], 3) if args.workload in PAPER_QPS else None,
         "dtype": "u32",
-        "data": "synthetic (seeded SplitMix64 table, uniform alpha, keys from pir_keygen)",
-        "config": {"workload": wk["desc"], "rows": rows, "width_words": width, "batch": batch, "n": n,
-                   "prf": "AES-128", "l2": f"inputs larger than L2: table {rows * width * 4 >> 20} MiB per step, no flush",
-                   "plan": plan.as_dict(), "parallelism": f"{world} replica(s), independent queries"},
+        "data": "synthetic (seeded SplitMix64 tables, uniform alpha, keys from pir_keygen)",
+        "config": cfg,
         "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
                        "p99": round(float(np.percentile(per_step, 99)), 4)},
         "gpu_launches": steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Glookup/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "fused_eval_kernel", "kernel_ms": round(kernel_ms, 4),
-                     "work": f"{LOOKUPS_PER_NODE} AES table lookups x {nodes} tree nodes per launch",
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(args.workload),
+                     "kernel": W.kernel, "kernel_ms": round(kernel_ms, 4),
+                     "work": f"{LOOKUPS_PER_NODE} AES table lookups x {W.nodes_per_step} tree nodes per launch",
                      "peak_basis": f"{sms} SMs x 32 shared-memory lookups/clk x {max_mhz:.0f} MHz (derived)"},
-        "e2e": {"value": round(batch * world * e2e_steps / (e2e_total / 1e3), 2), "unit": "queries/s",
-                "h2d_bytes_per_step": batch * kb, "d2h_bytes_per_step": batch * width * 4,
+        "e2e": {"value": round(W.queries_per_step * world * e2e_steps / (e2e_total / 1e3), 2), "unit": "queries/s",
+                "h2d_bytes_per_step": W.h2d_bytes, "d2h_bytes_per_step": W.d2h_bytes,
                 "p50_ms": round(float(np.percentile(e2e_ms, 50)), 4), "bit_exact_vs_device": e2e_ok},
         "selfcheck_reconstruct_all": selfcheck,
         "clocks": clocks,
     }
-    if materialised:
-        out["materialised"] = materialised
-    if plain_lat:
-        out["plain"] = {"qps": round(1e3 / statistics.mean(plain_lat), 2),
-                        "p50_ms": round(float(np.percentile(plain_lat, 50)), 4),
-                        "p99_ms": round(float(np.percentile(plain_lat, 99)), 4), "launches": len(plain_lat)}
+    out.update(extras)
     if world == 1 and not args.no_cpu_baseline:
-        qps, cores, nq, wall = oracle_qps(rows, width, seed, table.cpu().numpy().view(np.uint32))
-        out["cpu_baseline"] = {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
-                                         f"{cores} host threads, {wall:.1f} s wall"}
+        out["cpu_baseline"] = W.cpu_baseline()
     print(json.dumps(out), flush=True)
 
 
@@ -413,14 +567,43 @@ def run_reference(args):
     if rank != 0:
         return
     wk = WORKLOADS[args.workload]
-    rows, width = wk["rows"], wk["width"]
-    table_np = wl.table_u32(wk["seed"], rows, width)
     steps, warm = args.steps or 5, args.warmup
-    for _ in range(warm):
-        oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=2.0, max_wall_s=8.0)
+    if args.workload == "multi_table":
+        # the same Zipf mix over the 8 tables; each step a bounded sample of its queries
+        shapes = list(zip(wl.MULTI_TABLE_ROWS, wl.MULTI_TABLE_WIDTHS))
+        tables = [wl.table_u32(wk["seed"] * 100 + i, r, w) for i, (r, w) in enumerate(shapes)]
+        assign = wl.zipf_assignment(wk["seed"], len(shapes), wl.MULTI_TABLE_QUERIES)
+
+        def one_step(i):
+            from concurrent.futures import ThreadPoolExecutor
+
+            import oracle
+
+            threads = os.cpu_count() or 1
+            qs = [(i * 2 * threads + j) % len(assign) for j in range(2 * threads)]
+            keys = []
+            for q in qs:
+                t = assign[q]
+                n = wl.domain_bits(shapes[t][0])
+                r0, r1, c0 = wl.key_randomness(wk["seed"] + q, n, 1)[0]
+                keys.append((t, oracle.gen(n, q % shapes[t][0], 1, r0, r1, c0)[0]))
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda tk: oracle.answer(tk[1], tables[tk[0]]), keys))
+            return len(qs) / (time.perf_counter() - t0), threads, len(qs), time.perf_counter() - t0
+        rows = width = None
+    else:
+        rows, width = wk["rows"], wk["width"]
+        table_np = wl.table_u32(wk["seed"], rows, width)
+
+        def one_step(i, quick=False):
+            return oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=2.0 if quick else 4.0,
+                              max_wall_s=8.0 if quick else 12.0)
+    for i in range(warm):
+        one_step(i)
     times, queries, cores = [], 0, 1
-    for _ in range(steps):
-        qps, cores, nq, wall = oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=4.0, max_wall_s=12.0)
+    for i in range(steps):
+        qps, cores, nq, wall = one_step(warm + i)
         times.append(wall)
         queries += nq
     total = sum(times)

@@ -163,6 +163,66 @@ int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t doma
  * Errors: as pir_server_eval, plus PIR_ERR_UNSUPPORTED for the size limit. */
 int pir_server_eval_noalloc(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
 
+/* ---- many tables in one launch ------------------------------------- */
+
+/* Opaque launch plan for one batch of queries spread over several resident
+ * tables of uneven sizes and widths (batched execution, Sec. 3.2.1, across
+ * tables).  Holds a device-resident work list: items of (table, row range of
+ * 2^r rows, up to 8 queries of that table), r = min(ceil(log2 rows),
+ * item_log2).  Keys and shares of the batch are laid out back to back in
+ * query order; pir_multi_plan_layout reports the offsets. */
+typedef struct pir_multi_plan pir_multi_plan;
+
+/* tables: host array of `ntables` descriptors (device data, every width
+ * <= 512 words); table_of_key: host array, table index of each of the
+ * `batch` queries; item_log2: rows per work item as a power of two, 0 for
+ * the largest the kernel supports (15).  The tables must stay resident
+ * while the plan is used.  Allocates device memory for the work list (the
+ * plan owns it).  Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN, PIR_ERR_UNSUPPORTED
+ * (width), PIR_ERR_NOMEM, PIR_ERR_CUDA. */
+int pir_multi_plan_create(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                          uint32_t item_log2, pir_multi_plan** plan);
+
+void pir_multi_plan_destroy(pir_multi_plan* plan);
+
+/* Layout of a plan's batch (all outputs optional, host): key_offsets[q]
+ * (bytes) and out_offsets[q] (u32 words) for q < batch, the key buffer's
+ * total bytes, the share buffer's total words, the number of work items. */
+int pir_multi_plan_layout(const pir_multi_plan* plan, uint64_t* key_offsets, uint64_t* out_offsets,
+                          uint64_t* key_bytes_total, uint64_t* out_words_total, uint64_t* items);
+
+/* One persistent launch over the whole work list: for every query q,
+ * dout[out_offsets[q] .. + width of its table) = its share (Sec. 3.1, fused
+ * as in Sec. 3.2.4).  dkeys: device, 16-byte aligned, key q at
+ * key_offsets[q] with n = ceil(log2 rows) of its table.  dout (device) is
+ * overwritten; dstatus as for pir_server_eval_device.  Asynchronous and
+ * capturable in a CUDA graph (a memset of dout, a memset of the plan's item
+ * counter, one kernel).  One plan serves one stream at a time: concurrent
+ * launches of the same plan race on its item counter. */
+int pir_server_eval_multi(const pir_multi_plan* plan, const uint8_t* dkeys, uint32_t* dout, uint32_t* dstatus,
+                          void* stream);
+
+/* pir_server_eval_multi from host buffers: copies `keys` (host, the plan's
+ * key layout) to device staging owned by the plan (allocated on the first
+ * call), launches, and copies the shares to `out` (host, the plan's share
+ * layout); returns after `out` is filled. */
+int pir_server_eval_multi_host(pir_multi_plan* plan, const uint8_t* keys, uint32_t* out, void* stream);
+
+/* A CUDA graph holding pir_server_eval_multi for fixed buffers: replaying it
+ * evaluates whatever keys dkeys holds at launch time. */
+typedef struct pir_graph pir_graph;
+int pir_multi_graph_create(const pir_multi_plan* plan, const uint8_t* dkeys, uint32_t* dout, uint32_t* dstatus,
+                           pir_graph** graph);
+int pir_graph_launch(pir_graph* graph, void* stream);
+void pir_graph_destroy(pir_graph* graph);
+
+/* Autotuner: times pir_server_eval_multi for item_log2 = 15, 14, ..., 11 on
+ * the given batch (device keys and a device share buffer of the plan's
+ * layout; synchronizes `stream`) and returns the fastest in *best_item_log2
+ * (and its time per launch in *best_ms when non-null). */
+int pir_multi_autotune(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                       const uint8_t* dkeys, uint32_t* dout, void* stream, uint32_t* best_item_log2, float* best_ms);
+
 /* ---- materialised (unfused) baseline ------------------------------- */
 
 #define PIR_CONTRACT_IMAD 0  /* CUDA-core 32-bit multiply-add */

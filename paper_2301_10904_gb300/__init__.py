@@ -68,6 +68,19 @@ def _load():
                                                   vp]),
         "pir_contract_u32": (ctypes.c_int, [u32p, ctypes.c_uint64, ctypes.c_size_t, ctypes.POINTER(pir_table), u32p,
                                             ctypes.c_int, vp]),
+        "pir_multi_plan_create": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, vp, ctypes.c_size_t,
+                                                 ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+        "pir_multi_plan_destroy": (None, [vp]),
+        "pir_multi_plan_layout": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(ctypes.c_uint64),
+                                                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "pir_server_eval_multi": (ctypes.c_int, [vp, u8p, u32p, u32p, vp]),
+        "pir_server_eval_multi_host": (ctypes.c_int, [vp, u8p, u32p, vp]),
+        "pir_multi_graph_create": (ctypes.c_int, [vp, u8p, u32p, u32p, ctypes.POINTER(ctypes.c_void_p)]),
+        "pir_graph_launch": (ctypes.c_int, [vp, vp]),
+        "pir_graph_destroy": (None, [vp]),
+        "pir_multi_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, vp, ctypes.c_size_t, u8p,
+                                              u32p, vp, ctypes.POINTER(ctypes.c_uint32),
+                                              ctypes.POINTER(ctypes.c_float)]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
@@ -219,6 +232,105 @@ def pir_contract_u32(dshares, batch: int, table, dout, engine: int = PIR_CONTRAC
     _check(_lib.pir_contract_u32(dshares.data_ptr(), dshares.stride(0), batch, ctypes.byref(tb), dout.data_ptr(),
                                  engine, _stream(stream)), "pir_contract_u32")
     return dout
+
+
+def _tables_array(tables):
+    arr = (pir_table * len(tables))(*[table_of(t) for t in tables])
+    return arr
+
+
+class MultiPlan:
+    """Owner of a pir_multi_plan (see include/pir.h); `layout` holds the key
+    byte offsets, share word offsets and totals of the batch."""
+
+    def __init__(self, tables, table_of_key, item_log2: int = 0):
+        import numpy as np
+
+        self._tables = _tables_array(tables)
+        self.table_of_key = np.ascontiguousarray(table_of_key, dtype=np.uint32)
+        self.batch = int(self.table_of_key.size)
+        h = ctypes.c_void_p()
+        _check(_lib.pir_multi_plan_create(self._tables, len(tables), self.table_of_key.ctypes.data, self.batch,
+                                          item_log2, ctypes.byref(h)), "pir_multi_plan_create")
+        self.handle = h
+        self.key_offsets = np.zeros(self.batch, np.uint64)
+        self.out_offsets = np.zeros(self.batch, np.uint64)
+        kt, ot, it = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.pir_multi_plan_layout(h, self.key_offsets.ctypes.data, self.out_offsets.ctypes.data,
+                                          ctypes.byref(kt), ctypes.byref(ot), ctypes.byref(it)),
+               "pir_multi_plan_layout")
+        self.key_bytes_total, self.out_words_total, self.items = kt.value, ot.value, it.value
+
+    def close(self):
+        if self.handle:
+            _lib.pir_multi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pir_multi_plan_create(tables, table_of_key, item_log2: int = 0) -> MultiPlan:
+    return MultiPlan(tables, table_of_key, item_log2)
+
+
+def pir_server_eval_multi(plan: MultiPlan, dkeys, dout, dstatus=None, stream=None):
+    _check(_lib.pir_server_eval_multi(plan.handle, dkeys.data_ptr(), dout.data_ptr(),
+                                      dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
+           "pir_server_eval_multi")
+    return dout
+
+
+def pir_server_eval_multi_host(plan: MultiPlan, keys, out, stream=None):
+    """Host keys (plan layout; bytes, numpy or pinned tensor) -> host shares."""
+    kbuf = bytes(keys) if isinstance(keys, (bytes, bytearray)) else keys
+    kptr = _buf(kbuf) if isinstance(kbuf, bytes) else _host_ptr(kbuf)
+    _check(_lib.pir_server_eval_multi_host(plan.handle, kptr, _host_ptr(out), _stream(stream)),
+           "pir_server_eval_multi_host")
+    return out
+
+
+class Graph:
+    def __init__(self, plan: MultiPlan, dkeys, dout, dstatus=None):
+        h = ctypes.c_void_p()
+        _check(_lib.pir_multi_graph_create(plan.handle, dkeys.data_ptr(), dout.data_ptr(),
+                                           dstatus.data_ptr() if dstatus is not None else None, ctypes.byref(h)),
+               "pir_multi_graph_create")
+        self.handle = h
+        self._keep = (plan, dkeys, dout, dstatus)
+
+    def launch(self, stream=None):
+        _check(_lib.pir_graph_launch(self.handle, _stream(stream)), "pir_graph_launch")
+
+    def close(self):
+        if self.handle:
+            _lib.pir_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pir_multi_graph_create(plan: MultiPlan, dkeys, dout, dstatus=None) -> Graph:
+    return Graph(plan, dkeys, dout, dstatus)
+
+
+def pir_multi_autotune(tables, table_of_key, dkeys, dout, stream=None):
+    """Returns (best item_log2, ms per launch) measured on the given batch."""
+    import numpy as np
+
+    tk = np.ascontiguousarray(table_of_key, dtype=np.uint32)
+    arr = _tables_array(tables)
+    best, ms = ctypes.c_uint32(), ctypes.c_float()
+    _check(_lib.pir_multi_autotune(arr, len(tables), tk.ctypes.data, tk.size, dkeys.data_ptr(), dout.data_ptr(),
+                                   _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "pir_multi_autotune")
+    return best.value, ms.value
 
 
 def pir_plan_for(rows: int, width: int, batch: int) -> pir_plan:

@@ -6,19 +6,22 @@
 //   P(0,0) = root;  P(d,j) = AES_{P(d-1,j>>1)}((j&1) || 0^120) ^ C_t[j&1][d],
 //   t = lsb(P(d-1,j>>1));  y(j) = (-1)^sigma (word1(P(n,j)) + lsb(P(n,j)) * cw_out).
 //
-// Structure of one CTA (256 threads), which owns G queries x 2^r rows:
-//  1. lookup table: S-box derived in-kernel from GF(2^8), expanded to the
-//     column table Te0 with 32 interleaved copies so that lane l always reads
-//     bank l (conflict-free, 1 LDS per lookup, index formed with one PRMT).
-//  2. path: thread g walks query g from the root to the CTA's range node at
-//     depth n - r (one PRF per level).
-//  3. split: level by level in shared memory until each query has one
-//     subtree root per thread (SQ = 256/G threads per query).
+// Structure.  One CTA of 512 threads per SM, persistent over work items; an
+// item is G queries x 2^r consecutive rows.
+//  1. lookup tables, built once per CTA: the S-box derived from GF(2^8), the
+//     four AES column tables Te0..Te3 (Te_r = rotl(Te0, 8r)), each with 32
+//     lane-private copies so that lane l always reads bank l.  A lookup is one
+//     PRMT (forms (byte << 8) | 4l) plus one LDS; no rotations.
+//  2. per item, path: thread g walks query g from the root to the item's
+//     range node at depth n - r (one PRF per level).
+//  3. split: level by level in shared memory until each query has one subtree
+//     root per thread (SQ = 512/G threads per query).
 //  4. per-thread depth-first expansion of its subtree (the paper's
-//     memory-bounded traversal, Sec. 3.2.3, with the pending right siblings
-//     in a shared-memory stack: memory O(threads * depth), not O(L)).  Each
+//     memory-bounded traversal, Sec. 3.2.3), pending right siblings in a
+//     shared-memory stack: O(threads x depth) node storage, not O(L).  One
 //     PRF evaluation yields both children (one key schedule, two blocks that
-//     share their first two rounds' lookups).
+//     share their first two rounds' lookups); for leaves only the 5 output
+//     bytes that the share needs are computed in the last round.
 //  5. every kPairs leaf pairs the CTA stops and multiplies the fresh leaf
 //     shares of all G queries into register accumulators against the table
 //     rows they index, reading each row once for all G queries (Sec. 3.2.4).
@@ -35,15 +38,21 @@
 namespace pir {
 namespace dev {
 
-constexpr int kThreads = 256;
-constexpr int kRowBytes = 256;                  // one row per byte value x
-constexpr int kLookupBytes = 256 * kRowBytes;   // 64 KiB: [0,128) Te0 copies, [128,256) stack
-constexpr int kStackLevels = 8;                 // 256 rows x 8 slots / 256 threads
-constexpr int kMaxDfsDepth = kStackLevels + 1;  // levels a thread expands on its own
-constexpr int kPairs = 2;                       // leaf pairs per subtree between MAC phases
-constexpr int kYBufWords = 2048;                // two buffers of G x 2kPairs x SQ words
-constexpr int kHdrWords = 3 * 8;
-constexpr int kSmemBytes = kLookupBytes + 4 * kYBufWords + 4 * kHdrWords;
+constexpr int kThreads = 512;
+constexpr int kPlaneBytes = 256 * 256;                     // 256 rows x [32 copies of Te_a | 32 of Te_b]
+constexpr int kTablesBytes = 2 * kPlaneBytes;              // plane 0: Te0|Te1, plane 1: Te2|Te3
+constexpr int kStackLevels = 8;                            // pending siblings per thread
+constexpr int kMaxDfsDepth = kStackLevels + 1;             // levels a thread expands on its own
+constexpr int kStackOff = kTablesBytes;
+constexpr int kStackBytes = kStackLevels * kThreads * 16;  // 64 KiB
+constexpr int kPairs = 2;                                  // leaf pairs per subtree between MAC phases
+constexpr int kYOff = kStackOff + kStackBytes;
+constexpr int kYWords = 2 * 2 * kPairs * kThreads;         // two buffers of G x 2kPairs x SQ words
+constexpr int kHdrOff = kYOff + 4 * kYWords;
+constexpr int kMaxGroup = 8;
+constexpr int kHdrBytes = 32 * kMaxGroup;                  // per query: key ptr, out ptr, ok, party, cw_out
+constexpr int kItemOff = kHdrOff + kHdrBytes;              // work-item index broadcast (multi-table kernel)
+constexpr int kSmemBytes = kItemOff + 16;
 
 // The kernel's only shared memory; naming the array (not a pointer to it) in
 // every access lets the compiler address it as shared with an immediate base.
@@ -54,6 +63,7 @@ struct FusedParams {
     uint64_t row_lo, row_hi;
     uint64_t stride;
     uint64_t first_range;
+    uint64_t nitems;
     const uint8_t* keys;
     uint32_t* out;
     uint32_t* status;
@@ -68,6 +78,14 @@ struct FusedParams {
     uint64_t ld;
     uint32_t shares_vec;  // 1 when shares and ld allow 16-byte stores
 };
+
+struct QueryHdr {  // one per query slot of the current item, in shared memory
+    const uint8_t* key;
+    uint32_t* out;
+    uint32_t ok, party, cw_out, pad;
+};
+
+__device__ __forceinline__ QueryHdr* hdr_slot(int g) { return reinterpret_cast<QueryHdr*>(sm + kHdrOff) + g; }
 
 // ---------------------------------------------------------------- GF(2^8)
 __device__ __forceinline__ uint32_t xtime(uint32_t a) { return ((a << 1) ^ (0x1bu & (0u - (a >> 7)))) & 0xffu; }
@@ -98,108 +116,119 @@ __device__ uint32_t sbox_entry(uint32_t x) {
 }
 
 // ---------------------------------------------------------------- lookups
-// Row x of the lookup area holds Te0[x] at byte 4*l for every lane l, so the
-// address of lane l's copy of Te0[byte r of s] is (byte << 8) | 4l: one PRMT.
-#define LK(s, r) (*reinterpret_cast<const uint32_t*>(sm + __byte_perm((s), lane4, 0x5504u | ((r) << 4))))
-#define R8(x) __funnelshift_l((x), (x), 8)
-#define R16(x) __funnelshift_l((x), (x), 16)
-#define R24(x) __funnelshift_l((x), (x), 24)
-// S-box bytes sit in byte 1 of Te0: gather four of them into one word
-#define SB4(a, b, c, d) __byte_perm(__byte_perm((a), (b), 0x0051u), __byte_perm((c), (d), 0x5100u), 0x7610u)
+// Te_t[x] for this lane sits at plane(t)*64K + x*256 + (t&1)*128 + 4*lane:
+// one PRMT builds (x << 8) | (lane base), the plane offset is an immediate.
+#define LKT(s, r, t)                                                                      \
+    (*reinterpret_cast<const uint32_t*>(sm + ((t) >> 1) * kPlaneBytes +                 \
+                                        __byte_perm((s), ((t) & 1) ? lane4h : lane4, 0x5504u | ((r) << 4))))
+// main rounds: byte r of a column goes through Te_r
+#define LK(s, r) LKT(s, r, r)
+// S-box byte S(x) sits at byte p of Te_{(p+2)&3}[x]; gather four (one per byte position)
+#define SBG(a, b, c, d) __byte_perm(__byte_perm((a), (b), 0x0050u), __byte_perm((c), (d), 0x7200u), 0x7610u)
+// SubBytes+ShiftRows column: byte p from byte p of column (c+p)
+#define SBCOL(w0, w1, w2, w3) SBG(LKT(w0, 0, 2), LKT(w1, 1, 3), LKT(w2, 2, 0), LKT(w3, 3, 1))
 
-__device__ void build_lookup(int tid) {
-    uint32_t* words = reinterpret_cast<uint32_t*>(sm);
-    // staging of the 256 Te0 values in the spare halves of rows 0..7
-    {
+__device__ void build_tables(int tid) {
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sm + kStackOff);  // Te0 staged in the stack area
+    if (tid < 256) {
         const uint32_t s = sbox_entry((uint32_t)tid);
         const uint32_t s2 = xtime(s);
-        const uint32_t te = s2 | (s << 8) | (s << 16) | ((s2 ^ s) << 24);
-        words[(tid >> 5) * 64 + 32 + (tid & 31)] = te;
+        stage[tid] = s2 | (s << 8) | (s << 16) | ((s2 ^ s) << 24);
     }
     __syncthreads();
+    // 4 tables x 256 rows x 32 lane copies = 32768 words
 #pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
-        const int w = i * kThreads + tid;
-        const int x = w >> 5;
-        words[x * 64 + (w & 31)] = words[(x >> 5) * 64 + 32 + (x & 31)];
+    for (int i = 0; i < 32768 / kThreads; ++i) {
+        const int f = i * kThreads + tid;
+        const int t = f >> 13, x = (f >> 5) & 255, lane = f & 31;
+        const uint32_t v = stage[x];
+        const uint32_t rv = t ? __funnelshift_l(v, v, 8 * t) : v;
+        *reinterpret_cast<uint32_t*>(sm + (t >> 1) * kPlaneBytes + x * 256 + (t & 1) * 128 + lane * 4) = rv;
     }
     __syncthreads();
 }
 
-// Both children of node v, before the codewords: c_b = AES_v(b || 0^120).
-__device__ __forceinline__ void prf2(const uint32_t lane4, const uint4 v, uint4& c0, uint4& c1) {
+// Both children of node v before the codewords, c_b = AES_v(b || 0^120).
+// With `leaf` set only byte 0 of c_b.x and all of c_b.y are produced (the
+// control bit and the Z_2^32 word of a leaf); the rest is left undefined.
+__device__ __forceinline__ void prf2(const uint32_t lane4, const uint32_t lane4h, const uint4 v, const bool leaf,
+                                     uint4& c0, uint4& c1) {
     uint32_t k0 = v.x, k1 = v.y, k2 = v.z, k3 = v.w;
-    const uint32_t s0 = k0, s1 = k1, s2 = k2, s3 = k3;  // round-0 state (block b=0)
-    uint32_t t;
-#define KEYROUND(rc)                                                   \
-    t = SB4(LK(k3, 1), LK(k3, 2), LK(k3, 3), LK(k3, 0)) ^ (rc);        \
-    k0 ^= t;                                                           \
-    k1 ^= k0;                                                          \
-    k2 ^= k1;                                                          \
+    const uint32_t s0 = k0, s1 = k1, s2 = k2, s3 = k3;  // round-0 state of block b=0
+#define KEYROUND(rc)                                                                        \
+    k0 ^= SBG(LKT(k3, 1, 2), LKT(k3, 2, 3), LKT(k3, 3, 0), LKT(k3, 0, 1)) ^ (rc);           \
+    k1 ^= k0;                                                                               \
+    k2 ^= k1;                                                                               \
     k3 ^= k2;
     KEYROUND(0x01u)
     // round 1: only byte 0 of column 0 differs between the two blocks
-    const uint32_t x1 = R8(LK(s1, 1)) ^ R16(LK(s2, 2)) ^ R24(LK(s3, 3)) ^ k0;
+    const uint32_t x1 = LK(s1, 1) ^ LK(s2, 2) ^ LK(s3, 3) ^ k0;
     const uint32_t a0 = LK(s0, 0) ^ x1;
     const uint32_t b0 = LK(s0 ^ 1u, 0) ^ x1;
-    const uint32_t u1 = LK(s1, 0) ^ R8(LK(s2, 1)) ^ R16(LK(s3, 2)) ^ R24(LK(s0, 3)) ^ k1;
-    const uint32_t u2 = LK(s2, 0) ^ R8(LK(s3, 1)) ^ R16(LK(s0, 2)) ^ R24(LK(s1, 3)) ^ k2;
-    const uint32_t u3 = LK(s3, 0) ^ R8(LK(s0, 1)) ^ R16(LK(s1, 2)) ^ R24(LK(s2, 3)) ^ k3;
+    const uint32_t u1 = LK(s1, 0) ^ LK(s2, 1) ^ LK(s3, 2) ^ LK(s0, 3) ^ k1;
+    const uint32_t u2 = LK(s2, 0) ^ LK(s3, 1) ^ LK(s0, 2) ^ LK(s1, 3) ^ k2;
+    const uint32_t u3 = LK(s3, 0) ^ LK(s0, 1) ^ LK(s1, 2) ^ LK(s2, 3) ^ k3;
     KEYROUND(0x02u)
-    // round 2: columns 1..3 are shared, column 0 feeds one lookup per output column
-    const uint32_t z0 = R8(LK(u1, 1)) ^ R16(LK(u2, 2)) ^ R24(LK(u3, 3)) ^ k0;
-    const uint32_t z1 = LK(u1, 0) ^ R8(LK(u2, 1)) ^ R16(LK(u3, 2)) ^ k1;
-    const uint32_t z2 = LK(u2, 0) ^ R8(LK(u3, 1)) ^ R24(LK(u1, 3)) ^ k2;
-    const uint32_t z3 = LK(u3, 0) ^ R16(LK(u1, 2)) ^ R24(LK(u2, 3)) ^ k3;
-    uint32_t A0 = LK(a0, 0) ^ z0, A1 = R24(LK(a0, 3)) ^ z1, A2 = R16(LK(a0, 2)) ^ z2, A3 = R8(LK(a0, 1)) ^ z3;
-    uint32_t B0 = LK(b0, 0) ^ z0, B1 = R24(LK(b0, 3)) ^ z1, B2 = R16(LK(b0, 2)) ^ z2, B3 = R8(LK(b0, 1)) ^ z3;
+    // round 2: columns 1..3 are shared; column 0 feeds one lookup per output column
+    const uint32_t z0 = LK(u1, 1) ^ LK(u2, 2) ^ LK(u3, 3) ^ k0;
+    const uint32_t z1 = LK(u1, 0) ^ LK(u2, 1) ^ LK(u3, 2) ^ k1;
+    const uint32_t z2 = LK(u2, 0) ^ LK(u3, 1) ^ LK(u1, 3) ^ k2;
+    const uint32_t z3 = LK(u3, 0) ^ LK(u1, 2) ^ LK(u2, 3) ^ k3;
+    uint32_t A0 = LK(a0, 0) ^ z0, A1 = LK(a0, 3) ^ z1, A2 = LK(a0, 2) ^ z2, A3 = LK(a0, 1) ^ z3;
+    uint32_t B0 = LK(b0, 0) ^ z0, B1 = LK(b0, 3) ^ z1, B2 = LK(b0, 2) ^ z2, B3 = LK(b0, 1) ^ z3;
     const uint32_t rcon[7] = {0x04u, 0x08u, 0x10u, 0x20u, 0x40u, 0x80u, 0x1bu};
 #pragma unroll
     for (int r = 0; r < 7; ++r) {  // rounds 3..9
         KEYROUND(rcon[r])
-        const uint32_t a0n = LK(A0, 0) ^ R8(LK(A1, 1)) ^ R16(LK(A2, 2)) ^ R24(LK(A3, 3)) ^ k0;
-        const uint32_t a1n = LK(A1, 0) ^ R8(LK(A2, 1)) ^ R16(LK(A3, 2)) ^ R24(LK(A0, 3)) ^ k1;
-        const uint32_t a2n = LK(A2, 0) ^ R8(LK(A3, 1)) ^ R16(LK(A0, 2)) ^ R24(LK(A1, 3)) ^ k2;
-        const uint32_t a3n = LK(A3, 0) ^ R8(LK(A0, 1)) ^ R16(LK(A1, 2)) ^ R24(LK(A2, 3)) ^ k3;
-        const uint32_t b0n = LK(B0, 0) ^ R8(LK(B1, 1)) ^ R16(LK(B2, 2)) ^ R24(LK(B3, 3)) ^ k0;
-        const uint32_t b1n = LK(B1, 0) ^ R8(LK(B2, 1)) ^ R16(LK(B3, 2)) ^ R24(LK(B0, 3)) ^ k1;
-        const uint32_t b2n = LK(B2, 0) ^ R8(LK(B3, 1)) ^ R16(LK(B0, 2)) ^ R24(LK(B1, 3)) ^ k2;
-        const uint32_t b3n = LK(B3, 0) ^ R8(LK(B0, 1)) ^ R16(LK(B1, 2)) ^ R24(LK(B2, 3)) ^ k3;
+        const uint32_t a0n = LK(A0, 0) ^ LK(A1, 1) ^ LK(A2, 2) ^ LK(A3, 3) ^ k0;
+        const uint32_t a1n = LK(A1, 0) ^ LK(A2, 1) ^ LK(A3, 2) ^ LK(A0, 3) ^ k1;
+        const uint32_t a2n = LK(A2, 0) ^ LK(A3, 1) ^ LK(A0, 2) ^ LK(A1, 3) ^ k2;
+        const uint32_t a3n = LK(A3, 0) ^ LK(A0, 1) ^ LK(A1, 2) ^ LK(A2, 3) ^ k3;
+        const uint32_t b0n = LK(B0, 0) ^ LK(B1, 1) ^ LK(B2, 2) ^ LK(B3, 3) ^ k0;
+        const uint32_t b1n = LK(B1, 0) ^ LK(B2, 1) ^ LK(B3, 2) ^ LK(B0, 3) ^ k1;
+        const uint32_t b2n = LK(B2, 0) ^ LK(B3, 1) ^ LK(B0, 2) ^ LK(B1, 3) ^ k2;
+        const uint32_t b3n = LK(B3, 0) ^ LK(B0, 1) ^ LK(B1, 2) ^ LK(B2, 3) ^ k3;
         A0 = a0n; A1 = a1n; A2 = a2n; A3 = a3n;
         B0 = b0n; B1 = b1n; B2 = b2n; B3 = b3n;
     }
     KEYROUND(0x36u)
 #undef KEYROUND
     // round 10: SubBytes + ShiftRows + AddRoundKey
-    c0.x = SB4(LK(A0, 0), LK(A1, 1), LK(A2, 2), LK(A3, 3)) ^ k0;
-    c0.y = SB4(LK(A1, 0), LK(A2, 1), LK(A3, 2), LK(A0, 3)) ^ k1;
-    c0.z = SB4(LK(A2, 0), LK(A3, 1), LK(A0, 2), LK(A1, 3)) ^ k2;
-    c0.w = SB4(LK(A3, 0), LK(A0, 1), LK(A1, 2), LK(A2, 3)) ^ k3;
-    c1.x = SB4(LK(B0, 0), LK(B1, 1), LK(B2, 2), LK(B3, 3)) ^ k0;
-    c1.y = SB4(LK(B1, 0), LK(B2, 1), LK(B3, 2), LK(B0, 3)) ^ k1;
-    c1.z = SB4(LK(B2, 0), LK(B3, 1), LK(B0, 2), LK(B1, 3)) ^ k2;
-    c1.w = SB4(LK(B3, 0), LK(B0, 1), LK(B1, 2), LK(B2, 3)) ^ k3;
+    if (leaf) {
+        c0.x = LKT(A0, 0, 2) ^ k0;
+        c0.y = SBCOL(A1, A2, A3, A0) ^ k1;
+        c1.x = LKT(B0, 0, 2) ^ k0;
+        c1.y = SBCOL(B1, B2, B3, B0) ^ k1;
+        c0.z = c0.w = c1.z = c1.w = 0u;
+    } else {
+        c0.x = SBCOL(A0, A1, A2, A3) ^ k0;
+        c0.y = SBCOL(A1, A2, A3, A0) ^ k1;
+        c0.z = SBCOL(A2, A3, A0, A1) ^ k2;
+        c0.w = SBCOL(A3, A0, A1, A2) ^ k3;
+        c1.x = SBCOL(B0, B1, B2, B3) ^ k0;
+        c1.y = SBCOL(B1, B2, B3, B0) ^ k1;
+        c1.z = SBCOL(B2, B3, B0, B1) ^ k2;
+        c1.w = SBCOL(B3, B0, B1, B2) ^ k3;
+    }
 }
 
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
 
-// Children of v at depth d (1-based) of key `key`: AES plus C_{lsb(v)}[b][d].
-__device__ __forceinline__ void expand(uint32_t lane4, const uint8_t* key, uint32_t d, uint4 v,
-                                       uint4& c0, uint4& c1) {
-    prf2(lane4, v, c0, c1);
+// Children of v at depth d (1-based) of `key`: AES plus C_{lsb(v)}[b][d].
+__device__ __forceinline__ void expand(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
+                                       bool leaf, uint4& c0, uint4& c1) {
+    prf2(lane4, lane4h, v, leaf, c0, c1);
     const uint4* cw = reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) + 32u * (v.x & 1u));
     c0 = xor4(c0, __ldg(cw));
     c1 = xor4(c1, __ldg(cw + 1));
 }
 
-// Pending right sibling at relative level `lvl` (1..8) of thread `tid`:
-// slot (lvl-1)*256 + tid in the spare halves of the lookup rows.
+// Pending right sibling at relative level `lvl` (1..8) of thread `tid`.
 __device__ __forceinline__ uint4* stack_slot(int lvl, int tid) {
-    const int s = (lvl - 1) * kThreads + tid;
-    return reinterpret_cast<uint4*>(sm + (s >> 3) * kRowBytes + 128 + (s & 7) * 16);
+    return reinterpret_cast<uint4*>(sm + kStackOff) + (lvl - 1) * kThreads + tid;
 }
 
-template <int G, int VEC>
+template <int VEC>
 __device__ __forceinline__ void load_row(const uint32_t* p, uint32_t (&v)[VEC]) {
     if constexpr (VEC == 4) {
         const uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
@@ -225,7 +254,7 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
         const uint64_t row = r0 + ((uint64_t)l << m) + 2ull * kbase + j;
         if (row < p.row_lo || row >= p.row_hi) continue;
         uint32_t tv[VEC];
-        load_row<G, VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv);
+        load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const uint32_t y = yb[(g * 2 * kPairs + j) * SQ + l];
@@ -238,10 +267,9 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
 // Writes this thread's last 2*kc leaf shares (rows row_base .. row_base+2kc-1)
 // to the materialised share matrix.
 template <int G>
-__device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t* yb, uint32_t q, int g, int l,
+__device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t* yb, uint32_t* dst, int g, int l,
                                             uint64_t row_base, uint32_t kc) {
     constexpr int SQ = kThreads / G;
-    uint32_t* dst = p.shares + (uint64_t)q * p.ld;
     if (kc == 2 && p.shares_vec && row_base >= p.row_lo && row_base + 4 <= p.row_hi &&
         ((row_base - p.row_lo) & 3u) == 0) {
         uint4 v;
@@ -258,56 +286,53 @@ __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t
     }
 }
 
-// The whole CTA program.  MAT = false: fused share x table product (a1-a6).
-// MAT = true: expansion only, leaf shares written to p.shares (a7 baseline).
+// One work item: the queries in the header slots (set by the caller) over the
+// 2^r rows starting at r0.  MAT = false: fused share x table product (a1-a6);
+// MAT = true: expansion only, leaf shares written to each slot's `out`.
+// Ends with a barrier, so shared memory is free for the next item.
 template <int G, int VEC, bool MAT>
-__device__ __forceinline__ void eval_body(const FusedParams& p) {
+__device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     constexpr int SQ = kThreads / G;
-    constexpr int LOG_SQ = (SQ == 256) ? 8 : (SQ == 128) ? 7 : (SQ == 64) ? 6 : 5;
-    static_assert(G * 2 * kPairs * SQ * 2 <= kYBufWords, "share buffers exceed their region");
+    constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
+    static_assert(G * 2 * kPairs * SQ * 2 <= kYWords, "share buffers exceed their region");
+    static_assert(G <= kMaxGroup, "too many query slots");
 
     const int tid = threadIdx.x;
-    const uint32_t lane4 = (uint32_t)(tid & 31) << 2;
-    uint32_t* ybuf = reinterpret_cast<uint32_t*>(sm + kLookupBytes);
-    uint32_t* hdr = reinterpret_cast<uint32_t*>(sm + kLookupBytes + 4 * kYBufWords);  // ok[G], party[G], cwo[G]
-
-    const uint32_t qg = blockIdx.x % p.nqg;
-    const uint64_t r0 = (p.first_range + blockIdx.x / p.nqg) << p.range_log2;
+    const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
+    uint32_t* ybuf = reinterpret_cast<uint32_t*>(sm + kYOff);
     const int n = (int)p.n, r = (int)p.range_log2;
     const int sd = min(LOG_SQ, r - 1);
     const int m = r - sd;
 
-    build_lookup(tid);
-
-    // ---- key headers and the path to this CTA's range node ---------------
+    // ---- key headers and the path to this item's range node ---------------
     uint4* bufA = reinterpret_cast<uint4*>(ybuf);
     uint4* bufB = bufA + kThreads;
     if (tid < G) {
-        const uint32_t q = qg * G + tid;
+        QueryHdr* h = hdr_slot(tid);
         uint32_t ok = 0, party = 0, cwo = 0;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (q < p.batch) {
-            const uint8_t* key = p.keys + (uint64_t)q * p.key_bytes;
-            const uint4 h = __ldg(reinterpret_cast<const uint4*>(key));
-            ok = h.x == kKeyMagic && (h.y & 0xffu) == kKeyVersion && ((h.y >> 8) & 0xffu) == p.n &&
-                 ((h.y >> 16) & 0xffu) <= 1u && (h.y >> 24) == 0u;
+        if (h->key) {
+            const uint8_t* key = h->key;
+            const uint4 hw = __ldg(reinterpret_cast<const uint4*>(key));
+            ok = hw.x == kKeyMagic && (hw.y & 0xffu) == kKeyVersion && ((hw.y >> 8) & 0xffu) == p.n &&
+                 ((hw.y >> 16) & 0xffu) <= 1u && (hw.y >> 24) == 0u;
             if (ok) {
-                party = (h.y >> 16) & 1u;
-                cwo = h.z;
+                party = (hw.y >> 16) & 1u;
+                cwo = hw.z;
                 v = __ldg(reinterpret_cast<const uint4*>(key + 16));
                 for (int d = 1; d <= n - r; ++d) {
                     const uint32_t b = (uint32_t)(r0 >> (n - d)) & 1u;
                     uint4 c0, c1;
-                    expand(lane4, key, (uint32_t)d, v, c0, c1);
+                    expand(lane4, lane4h, key, (uint32_t)d, v, false, c0, c1);
                     v = b ? c1 : c0;
                 }
             } else if (p.status) {
                 atomicOr(p.status, PIR_STATUS_BAD_KEY);
             }
         }
-        hdr[tid] = ok;
-        hdr[G + tid] = party;
-        hdr[2 * G + tid] = cwo;
+        h->ok = ok;
+        h->party = party;
+        h->cw_out = cwo;
         bufA[tid] = v;
     }
     __syncthreads();
@@ -320,10 +345,8 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
             const int g = tid >> i, idx = tid & ((1 << i) - 1);
             const uint4 v = src[tid];
             uint4 c0 = v, c1 = v;
-            if (hdr[g]) {
-                const uint8_t* key = p.keys + (uint64_t)(qg * G + g) * p.key_bytes;
-                expand(lane4, key, (uint32_t)(n - r + i + 1), v, c0, c1);
-            }
+            const QueryHdr* h = hdr_slot(g);
+            if (h->ok) expand(lane4, lane4h, h->key, (uint32_t)(n - r + i + 1), v, false, c0, c1);
             dst[(g << (i + 1)) + 2 * idx] = c0;
             dst[(g << (i + 1)) + 2 * idx + 1] = c1;
         }
@@ -331,11 +354,12 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
     }
     const int g = tid / SQ, l = tid % SQ;
     const int nsub = 1 << sd;
-    const bool act = l < nsub && hdr[g] != 0;
-    const uint32_t party = hdr[G + g], cwo = hdr[2 * G + g];
+    const QueryHdr* hq = hdr_slot(g);
+    const bool act = l < nsub && hq->ok != 0;
+    const uint32_t party = hq->party, cwo = hq->cw_out;
+    const uint8_t* key = hq->key;
     uint4 node = make_uint4(0, 0, 0, 0);
     if (l < nsub) node = ((sd & 1) ? bufB : bufA)[(g << sd) + l];
-    const uint8_t* key = p.keys + (uint64_t)(qg * G + (act ? g : 0)) * p.key_bytes;
     __syncthreads();  // share buffers alias the split buffers
 
     // ---- depth-first expansion with periodic table products ----------------
@@ -351,9 +375,10 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
     int lvl = 0;
     uint32_t k = 0, phase = 0;
     for (;;) {
+        const bool leaf = lvl + 1 == m;
         uint4 c0 = node, c1 = node;
-        if (act) expand(lane4, key, (uint32_t)(d0 + lvl + 1), node, c0, c1);
-        if (lvl + 1 == m) {
+        if (act) expand(lane4, lane4h, key, (uint32_t)(d0 + lvl + 1), node, leaf, c0, c1);
+        if (leaf) {
             uint32_t y0 = 0, y1 = 0;
             if (act) {
                 y0 = c0.y + (c0.x & 1u) * cwo;
@@ -363,7 +388,7 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
                     y1 = 0u - y1;
                 }
             }
-            uint32_t* yb = ybuf + (phase & 1u) * (kYBufWords / 2);
+            uint32_t* yb = ybuf + (phase & 1u) * (kYWords / 2);
             const uint32_t j = 2u * (k % kc);
             yb[(g * 2 * kPairs + j) * SQ + l] = y0;
             yb[(g * 2 * kPairs + j + 1) * SQ + l] = y1;
@@ -371,9 +396,8 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
             if (k % kc == 0) {
                 if constexpr (MAT) {
                     // each thread stores only what it wrote itself: no barrier needed
-                    const uint32_t q = qg * G + g;
-                    if (q < p.batch && l < nsub)
-                        store_phase<G>(p, yb, q, g, l, r0 + ((uint64_t)l << m) + 2ull * (k - kc), kc);
+                    if (hq->out && l < nsub)
+                        store_phase<G>(p, yb, hq->out, g, l, r0 + ((uint64_t)l << m) + 2ull * (k - kc), kc);
                 } else {
                     __syncthreads();
                     mac_phase<G, VEC>(p, yb, r0, m, sd, k - kc, kc, acc, tid);
@@ -390,9 +414,9 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
         }
     }
 
+    __syncthreads();
     if constexpr (MAT) return;
     // ---- reduce the per-thread partial sums, then one atomic per word ------
-    __syncthreads();
     const uint32_t W = p.width;
     uint32_t* red = ybuf;
     for (uint32_t i = tid; i < G * W; i += kThreads) red[i] = 0;
@@ -410,20 +434,80 @@ __device__ __forceinline__ void eval_body(const FusedParams& p) {
     }
     __syncthreads();
     for (uint32_t i = tid; i < G * W; i += kThreads) {
-        const uint32_t a = i / W, q = qg * G + a;
+        const uint32_t a = i / W;
         const uint32_t v = red[i];
-        if (q < p.batch && v) atomicAdd(&p.out[(uint64_t)q * W + (i - a * W)], v);
+        uint32_t* o = hdr_slot((int)a)->out;
+        if (o && v) atomicAdd(o + (i - a * W), v);
+    }
+    __syncthreads();
+}
+
+// Persistent grid over items (query group, row range), query groups fastest so
+// that items running at the same time share table rows through L2.
+template <int G, int VEC, bool MAT>
+__device__ __forceinline__ void eval_items(const FusedParams& p) {
+    build_tables(threadIdx.x);
+    for (uint64_t item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+        const uint32_t qg = (uint32_t)(item % p.nqg);
+        const uint64_t r0 = (p.first_range + item / p.nqg) << p.range_log2;
+        if (threadIdx.x < G) {
+            const uint32_t q = qg * G + threadIdx.x;
+            QueryHdr* h = hdr_slot(threadIdx.x);
+            const bool valid = q < p.batch;
+            h->key = valid ? p.keys + (uint64_t)q * p.key_bytes : nullptr;
+            if constexpr (MAT)
+                h->out = valid ? p.shares + (uint64_t)q * p.ld : nullptr;
+            else
+                h->out = valid ? p.out + (uint64_t)q * p.width : nullptr;
+        }
+        __syncthreads();
+        run_item<G, VEC, MAT>(p, r0);
     }
 }
 
 template <int G, int VEC>
-__global__ void __launch_bounds__(kThreads, 3) fused_eval_kernel(const FusedParams p) {
-    eval_body<G, VEC, false>(p);
+__global__ void __launch_bounds__(kThreads, 1) fused_eval_kernel(const FusedParams p) {
+    eval_items<G, VEC, false>(p);
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads, 3) expand_materialise_kernel(const FusedParams p) {
-    eval_body<G, 1, true>(p);
+__global__ void __launch_bounds__(kThreads, 1) expand_materialise_kernel(const FusedParams p) {
+    eval_items<G, 1, true>(p);
+}
+
+// Many tables of different sizes and widths in one launch.  Items are
+// (table, row range, up to 8 queries of that table); CTAs take the next item
+// from a counter, so uneven items balance themselves.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads, 1) multi_eval_kernel(const MultiParams mp) {
+    build_tables(threadIdx.x);
+    uint64_t* s_item = reinterpret_cast<uint64_t*>(sm + kItemOff);
+    for (;;) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(reinterpret_cast<unsigned long long*>(mp.counter), 1ull);
+        __syncthreads();
+        const uint64_t it = *s_item;  // every thread reads it before run_item's first barrier
+        if (it >= mp.nitems) break;
+        const MultiItem& w = mp.items[it];
+        const MultiTable& tb = mp.tables[w.table];
+        FusedParams p{};
+        p.table = tb.data;
+        p.row_lo = 0;
+        p.row_hi = tb.rows;
+        p.stride = tb.stride;
+        p.status = mp.status;
+        p.key_bytes = tb.key_bytes;
+        p.width = tb.width;
+        p.n = tb.n;
+        p.range_log2 = tb.range_log2;
+        if (threadIdx.x < kMaxGroup) {
+            const uint32_t q = w.q[threadIdx.x];
+            QueryHdr* h = hdr_slot(threadIdx.x);
+            h->key = q != kNoQuery ? mp.keys + mp.key_off[q] : nullptr;
+            h->out = q != kNoQuery ? mp.out + mp.out_off[q] : nullptr;
+        }
+        __syncthreads();
+        run_item<kMaxGroup, VEC, false>(p, w.range << tb.range_log2);
+    }
 }
 
 template <typename Kern>
@@ -433,11 +517,6 @@ cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, cudaSt
     if (e != cudaSuccess) return e;
     kern<<<ctas, kThreads, kSmemBytes, s>>>(p);
     return cudaGetLastError();
-}
-
-template <int G, int VEC>
-cudaError_t launch_one(const FusedParams& p, uint32_t ctas, cudaStream_t s) {
-    return launch_kernel(fused_eval_kernel<G, VEC>, p, ctas, s);
 }
 
 }  // namespace dev
@@ -451,9 +530,14 @@ int device_sm_count() {
     return sms;
 }
 
-static int log_sq(uint32_t group) { return group == 1 ? 8 : group == 2 ? 7 : group == 4 ? 6 : 5; }
+static int log_sq(uint32_t group) {
+    const int sq = dev::kThreads / (int)group;
+    int l = 0;
+    while ((1 << l) < sq) ++l;
+    return l;
+}
 
-static uint64_t ctas_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t nqg) {
+static uint64_t items_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t nqg) {
     if (rows == 0) return 0;
     const uint64_t first = row_lo >> r, last = (row_lo + rows - 1) >> r;
     return (last - first + 1) * nqg;
@@ -464,7 +548,7 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     if (plan.vec != 1 && plan.vec != 4) return PIR_ERR_UNSUPPORTED;
     if (plan.vec == 4 && (!vec_ok || width % 4 != 0)) return PIR_ERR_UNSUPPORTED;
     if (width == 0 || width / plan.vec > (uint32_t)dev::kThreads) return PIR_ERR_UNSUPPORTED;
-    if ((uint64_t)plan.group * width > (uint64_t)dev::kYBufWords) return PIR_ERR_UNSUPPORTED;
+    if ((uint64_t)plan.group * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
     const int r = (int)plan.range_log2;
     if (r < 1 || r > (int)n) return PIR_ERR_UNSUPPORTED;
     const int sd = std::min(log_sq(plan.group), r - 1);
@@ -479,17 +563,20 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     pl.vec = (vec_ok && width % 4 == 0) ? 4 : 1;
     if (width / pl.vec > (uint32_t)dev::kThreads) return PIR_ERR_UNSUPPORTED;
     uint32_t g = 8;
-    while (g > 1 && (g > batch || (uint64_t)g * width > (uint64_t)dev::kYBufWords)) g >>= 1;
-    if ((uint64_t)g * width > (uint64_t)dev::kYBufWords) return PIR_ERR_UNSUPPORTED;
+    while (g > 1 && (g > batch || (uint64_t)g * width > (uint64_t)dev::kYWords)) g >>= 1;
+    if ((uint64_t)g * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
     pl.group = g;
     const uint32_t nqg = (batch + g - 1) / g;
     const int lsq = log_sq(g);
     int r = std::min((int)n, lsq + dev::kMaxDfsDepth);
     const int sms = std::max(1, device_sm_count());
-    const uint64_t target = (uint64_t)sms * 3 * 4;  // about four waves of resident CTAs
-    while (r > std::min((int)n, lsq + 1) && ctas_for(row_lo, rows, (uint32_t)r, nqg) < target) --r;
+    // batches: shrink the items until there are about six per SM (balance of the last
+    // round); a few queries: about one item per SM (each item repeats the path walk)
+    const uint64_t target = (uint64_t)sms * (batch >= 8 ? 6 : 1);
+    while (r > std::min((int)n, lsq + 1) && items_for(row_lo, rows, (uint32_t)r, nqg) < target) --r;
     pl.range_log2 = (uint32_t)r;
-    pl.ctas = (uint32_t)ctas_for(row_lo, rows, (uint32_t)r, nqg);
+    const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
+    pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
     *plan = pl;
     return PIR_OK;
 }
@@ -510,7 +597,13 @@ static dev::FusedParams make_params(const EvalRequest& req, const pir_plan& plan
     p.n = req.n;
     p.range_log2 = plan.range_log2;
     p.nqg = (req.batch + plan.group - 1) / plan.group;
+    p.nitems = items_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
     return p;
+}
+
+static uint32_t grid_for(uint64_t items) {
+    const int sms = std::max(1, device_sm_count());
+    return (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
 }
 
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream) {
@@ -518,42 +611,54 @@ int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* s
     p.shares = shares;
     p.ld = ld;
     p.shares_vec = ((reinterpret_cast<uintptr_t>(shares) & 15u) == 0 && ld % 4 == 0) ? 1u : 0u;
-    const uint64_t ctas = ctas_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
-    if (ctas == 0) return PIR_OK;
-    if (ctas > 0x7fffffffull) return PIR_ERR_UNSUPPORTED;
+    if (p.nitems == 0) return PIR_OK;
+    const uint32_t ctas = grid_for(p.nitems);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
     switch (plan.group) {
-        case 1: e = dev::launch_kernel(dev::expand_materialise_kernel<1>, p, (uint32_t)ctas, s); break;
-        case 2: e = dev::launch_kernel(dev::expand_materialise_kernel<2>, p, (uint32_t)ctas, s); break;
-        case 4: e = dev::launch_kernel(dev::expand_materialise_kernel<4>, p, (uint32_t)ctas, s); break;
-        default: e = dev::launch_kernel(dev::expand_materialise_kernel<8>, p, (uint32_t)ctas, s); break;
+        case 1: e = dev::launch_kernel(dev::expand_materialise_kernel<1>, p, ctas, s); break;
+        case 2: e = dev::launch_kernel(dev::expand_materialise_kernel<2>, p, ctas, s); break;
+        case 4: e = dev::launch_kernel(dev::expand_materialise_kernel<4>, p, ctas, s); break;
+        default: e = dev::launch_kernel(dev::expand_materialise_kernel<8>, p, ctas, s); break;
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "expand_materialise launch");
 }
 
+int multi_group() { return dev::kMaxGroup; }
+int multi_max_range_log2() { return log_sq(dev::kMaxGroup) + dev::kMaxDfsDepth; }
+
+int launch_multi(const MultiParams& mp, bool vec, void* stream) {
+    if (mp.nitems == 0) return PIR_OK;
+    const uint32_t ctas = grid_for(mp.nitems);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto kern = vec ? dev::multi_eval_kernel<4> : dev::multi_eval_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kSmemBytes);
+    if (e == cudaSuccess) {
+        kern<<<ctas, dev::kThreads, dev::kSmemBytes, s>>>(mp);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "multi_eval launch");
+}
+
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
-    const uint32_t g = plan.group;
-    dev::FusedParams p = make_params(req, plan);
-    const uint64_t ctas = ctas_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
-    if (ctas == 0) return PIR_OK;
-    if (ctas > 0x7fffffffull) return PIR_ERR_UNSUPPORTED;
+    const dev::FusedParams p = make_params(req, plan);
+    if (p.nitems == 0) return PIR_OK;
+    const uint32_t ctas = grid_for(p.nitems);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    const uint32_t c = (uint32_t)ctas;
     if (plan.vec == 4) {
-        switch (g) {
-            case 1: e = dev::launch_one<1, 4>(p, c, s); break;
-            case 2: e = dev::launch_one<2, 4>(p, c, s); break;
-            case 4: e = dev::launch_one<4, 4>(p, c, s); break;
-            default: e = dev::launch_one<8, 4>(p, c, s); break;
+        switch (plan.group) {
+            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 4>, p, ctas, s); break;
+            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 4>, p, ctas, s); break;
+            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 4>, p, ctas, s); break;
+            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 4>, p, ctas, s); break;
         }
     } else {
-        switch (g) {
-            case 1: e = dev::launch_one<1, 1>(p, c, s); break;
-            case 2: e = dev::launch_one<2, 1>(p, c, s); break;
-            case 4: e = dev::launch_one<4, 1>(p, c, s); break;
-            default: e = dev::launch_one<8, 1>(p, c, s); break;
+        switch (plan.group) {
+            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 1>, p, ctas, s); break;
+            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 1>, p, ctas, s); break;
+            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 1>, p, ctas, s); break;
+            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 1>, p, ctas, s); break;
         }
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "fused_eval launch");

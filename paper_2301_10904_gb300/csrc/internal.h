@@ -38,6 +38,38 @@ struct EvalRequest {
     uint32_t* dstatus;    // optional
 };
 
+// ---- multi-table work list (multi.cpp builds it, dpf_eval.cu runs it) --------
+constexpr uint32_t kNoQuery = 0xffffffffu;
+struct MultiTable {  // device copy of one registered table
+    const uint32_t* data;
+    uint64_t rows;
+    uint64_t stride;
+    uint32_t width;
+    uint32_t n;
+    uint32_t key_bytes;
+    uint32_t range_log2;  // rows per item of this table: 2^range_log2
+};
+struct MultiItem {  // (table, row range, up to 8 queries of that table)
+    uint32_t table;
+    uint32_t pad;
+    uint64_t range;  // first row = range << range_log2
+    uint32_t q[8];   // query indices, kNoQuery for empty slots
+};
+struct MultiParams {
+    const MultiTable* tables;
+    const MultiItem* items;
+    uint64_t nitems;
+    const uint64_t* key_off;  // byte offset of key q in keys
+    const uint64_t* out_off;  // word offset of share q in out
+    const uint8_t* keys;
+    uint32_t* out;
+    uint32_t* status;
+    uint64_t* counter;  // next item; zeroed before each launch
+};
+int launch_multi(const MultiParams& mp, bool vec, void* stream);
+int multi_group();          // queries per item
+int multi_max_range_log2(); // largest rows-per-item exponent the kernel supports
+
 int device_sm_count();
 int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan);

@@ -1,0 +1,314 @@
+// Many queries against many resident tables of uneven sizes and widths in one
+// persistent launch (the batched form of Sec. 3.2.1 extended across tables),
+// and CUDA-graph capture of that launch.
+//
+// The planner groups each table's queries by eights and cuts the table into
+// row ranges of 2^r rows, one work item per (range, group).  Every table gets
+// the same rows per item where it can (2^item_log2, clipped to the table), so
+// items cost about the same and the kernel's item counter balances the rest.
+// Items of one table range are adjacent, so the items in flight at any moment
+// share table rows through L2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+struct pir_multi_plan {
+    int device = -1;
+    uint32_t batch = 0;
+    uint32_t item_log2 = 0;
+    bool vec = true;
+    std::vector<uint64_t> key_off, out_off;
+    uint64_t key_total = 0, out_total = 0, nitems = 0;
+    pir::MultiTable* d_tables = nullptr;
+    pir::MultiItem* d_items = nullptr;
+    uint64_t* d_key_off = nullptr;
+    uint64_t* d_out_off = nullptr;
+    uint64_t* d_counter = nullptr;
+    uint8_t* d_stage_keys = nullptr;  // host-buffer entry point staging, allocated on first use
+    uint32_t* d_stage_out = nullptr;
+};
+
+struct pir_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace pir {
+namespace {
+
+void free_plan(pir_multi_plan* p) {
+    if (!p) return;
+    cudaFree(p->d_tables);
+    cudaFree(p->d_items);
+    cudaFree(p->d_key_off);
+    cudaFree(p->d_out_off);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_stage_keys);
+    cudaFree(p->d_stage_out);
+    delete p;
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+    const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return cuda_fail((int)e, "multi plan alloc");
+    if (!src.empty()) {
+        e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail((int)e, "multi plan upload");
+    }
+    return PIR_OK;
+}
+
+}  // namespace
+}  // namespace pir
+
+extern "C" {
+
+int pir_multi_plan_create(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                          uint32_t item_log2, pir_multi_plan** out_plan) {
+    using namespace pir;
+    if (!tables || ntables == 0 || ntables > 0xffffffffu || !table_of_key || batch == 0 || batch > 0xfffffffeu ||
+        !out_plan)
+        return PIR_ERR_ARG;
+    *out_plan = nullptr;
+    const int G = multi_group();
+    const int rmax = multi_max_range_log2();
+    if (item_log2 == 0) item_log2 = (uint32_t)rmax;
+    if ((int)item_log2 > rmax) return PIR_ERR_UNSUPPORTED;
+
+    pir_multi_plan* plan = new (std::nothrow) pir_multi_plan();
+    if (!plan) return PIR_ERR_NOMEM;
+    plan->batch = (uint32_t)batch;
+    plan->item_log2 = item_log2;
+    cudaGetDevice(&plan->device);
+
+    std::vector<MultiTable> mt(ntables);
+    for (size_t t = 0; t < ntables; ++t) {
+        const pir_table& tb = tables[t];
+        if (!tb.data || tb.rows < 1 || tb.width < 1 || tb.stride < tb.width ||
+            (reinterpret_cast<uintptr_t>(tb.data) & 3u) != 0) {
+            free_plan(plan);
+            return PIR_ERR_ARG;
+        }
+        if ((uint64_t)G * tb.width > 4096u || tb.width > 512u) {
+            free_plan(plan);
+            return PIR_ERR_UNSUPPORTED;
+        }
+        const uint32_t n = pir_domain_bits(tb.rows);
+        if (n == 0) {
+            free_plan(plan);
+            return PIR_ERR_DOMAIN;
+        }
+        plan->vec = plan->vec && (reinterpret_cast<uintptr_t>(tb.data) & 15u) == 0 && tb.stride % 4 == 0 &&
+                    tb.width % 4 == 0;
+        mt[t].data = tb.data;
+        mt[t].rows = tb.rows;
+        mt[t].stride = tb.stride;
+        mt[t].width = tb.width;
+        mt[t].n = n;
+        mt[t].key_bytes = (uint32_t)key_bytes(n);
+        mt[t].range_log2 = std::min<uint32_t>(n, item_log2);
+    }
+    // offsets of keys and shares in query order; queries grouped per table
+    plan->key_off.resize(batch);
+    plan->out_off.resize(batch);
+    std::vector<std::vector<uint32_t>> per_table(ntables);
+    for (size_t q = 0; q < batch; ++q) {
+        const uint32_t t = table_of_key[q];
+        if (t >= ntables) {
+            free_plan(plan);
+            return PIR_ERR_ARG;
+        }
+        plan->key_off[q] = plan->key_total;
+        plan->out_off[q] = plan->out_total;
+        plan->key_total += mt[t].key_bytes;
+        plan->out_total += mt[t].width;
+        per_table[t].push_back((uint32_t)q);
+    }
+    std::vector<MultiItem> items;
+    for (size_t t = 0; t < ntables; ++t) {
+        const auto& qs = per_table[t];
+        if (qs.empty()) continue;
+        const uint64_t ranges = ((mt[t].rows - 1) >> mt[t].range_log2) + 1;
+        const size_t groups = (qs.size() + G - 1) / G;
+        for (uint64_t rg = 0; rg < ranges; ++rg) {
+            for (size_t gi = 0; gi < groups; ++gi) {
+                MultiItem it{};
+                it.table = (uint32_t)t;
+                it.range = rg;
+                for (int s = 0; s < 8; ++s) {
+                    const size_t idx = gi * G + s;
+                    it.q[s] = (s < G && idx < qs.size()) ? qs[idx] : kNoQuery;
+                }
+                items.push_back(it);
+            }
+        }
+    }
+    plan->nitems = items.size();
+    int rc = upload(&plan->d_tables, mt);
+    if (rc == PIR_OK) rc = upload(&plan->d_items, items);
+    if (rc == PIR_OK) rc = upload(&plan->d_key_off, plan->key_off);
+    if (rc == PIR_OK) rc = upload(&plan->d_out_off, plan->out_off);
+    if (rc == PIR_OK) {
+        cudaError_t e = cudaMalloc((void**)&plan->d_counter, sizeof(uint64_t));
+        if (e != cudaSuccess) rc = cuda_fail((int)e, "multi plan counter");
+    }
+    if (rc != PIR_OK) {
+        free_plan(plan);
+        return rc;
+    }
+    *out_plan = plan;
+    return PIR_OK;
+}
+
+void pir_multi_plan_destroy(pir_multi_plan* plan) { pir::free_plan(plan); }
+
+int pir_multi_plan_layout(const pir_multi_plan* plan, uint64_t* key_offsets, uint64_t* out_offsets,
+                          uint64_t* key_bytes_total, uint64_t* out_words_total, uint64_t* items) {
+    if (!plan) return PIR_ERR_ARG;
+    if (key_offsets) std::memcpy(key_offsets, plan->key_off.data(), plan->batch * sizeof(uint64_t));
+    if (out_offsets) std::memcpy(out_offsets, plan->out_off.data(), plan->batch * sizeof(uint64_t));
+    if (key_bytes_total) *key_bytes_total = plan->key_total;
+    if (out_words_total) *out_words_total = plan->out_total;
+    if (items) *items = plan->nitems;
+    return PIR_OK;
+}
+
+int pir_server_eval_multi(const pir_multi_plan* plan, const uint8_t* dkeys, uint32_t* dout, uint32_t* dstatus,
+                          void* stream) {
+    using namespace pir;
+    if (!plan || !dkeys || !dout || (reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(dout, 0, plan->out_total * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "multi memset");
+    MultiParams mp{};
+    mp.tables = plan->d_tables;
+    mp.items = plan->d_items;
+    mp.nitems = plan->nitems;
+    mp.key_off = plan->d_key_off;
+    mp.out_off = plan->d_out_off;
+    mp.keys = dkeys;
+    mp.out = dout;
+    mp.status = dstatus;
+    mp.counter = plan->d_counter;
+    return launch_multi(mp, plan->vec, stream);
+}
+
+int pir_server_eval_multi_host(pir_multi_plan* plan, const uint8_t* keys, uint32_t* out, void* stream) {
+    using namespace pir;
+    if (!plan || !keys || !out) return PIR_ERR_ARG;
+    if (!plan->d_stage_keys) {
+        cudaError_t e = cudaMalloc((void**)&plan->d_stage_keys, std::max<uint64_t>(16, plan->key_total));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void**)&plan->d_stage_out, std::max<uint64_t>(1, plan->out_total) * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_fail((int)e, "multi staging alloc");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(plan->d_stage_keys, keys, plan->key_total, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "multi copy keys");
+    int rc = pir_server_eval_multi(plan, plan->d_stage_keys, plan->d_stage_out, nullptr, stream);
+    if (rc != PIR_OK) return rc;
+    e = cudaMemcpyAsync(out, plan->d_stage_out, plan->out_total * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "multi copy shares");
+}
+
+int pir_multi_graph_create(const pir_multi_plan* plan, const uint8_t* dkeys, uint32_t* dout, uint32_t* dstatus,
+                           pir_graph** out_graph) {
+    using namespace pir;
+    if (!plan || !out_graph) return PIR_ERR_ARG;
+    *out_graph = nullptr;
+    pir_graph* g = new (std::nothrow) pir_graph();
+    if (!g) return PIR_ERR_NOMEM;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail((int)e, "graph stream");
+    }
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "begin capture");
+    if (rc == PIR_OK) {
+        rc = pir_server_eval_multi(plan, dkeys, dout, dstatus, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
+        if (rc == PIR_OK && e2 != cudaSuccess) rc = cuda_fail((int)e2, "end capture");
+    }
+    if (rc == PIR_OK) {
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail((int)e, "graph instantiate");
+    }
+    cudaStreamDestroy(s);
+    if (rc != PIR_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    *out_graph = g;
+    return PIR_OK;
+}
+
+int pir_graph_launch(pir_graph* g, void* stream) {
+    if (!g || !g->exec) return PIR_ERR_ARG;
+    cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PIR_OK : pir::cuda_fail((int)e, "graph launch");
+}
+
+void pir_graph_destroy(pir_graph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+int pir_multi_autotune(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                       const uint8_t* dkeys, uint32_t* dout, void* stream, uint32_t* best_item_log2,
+                       float* best_ms) {
+    using namespace pir;
+    if (!best_item_log2) return PIR_ERR_ARG;
+    const int rmax = multi_max_range_log2();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 0.f;
+    uint32_t best_r = 0;
+    int rc = PIR_OK;
+    for (int r = rmax; r >= rmax - 4 && r >= 8; --r) {
+        pir_multi_plan* plan = nullptr;
+        rc = pir_multi_plan_create(tables, ntables, table_of_key, batch, (uint32_t)r, &plan);
+        if (rc != PIR_OK) break;
+        rc = pir_server_eval_multi(plan, dkeys, dout, nullptr, stream);  // warm-up
+        float ms = 0.f;
+        if (rc == PIR_OK) {
+            cudaEventRecord(a, s);
+            for (int i = 0; i < 3 && rc == PIR_OK; ++i) rc = pir_server_eval_multi(plan, dkeys, dout, nullptr, stream);
+            cudaEventRecord(b, s);
+            cudaError_t e = cudaEventSynchronize(b);
+            if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "autotune sync");
+            cudaEventElapsedTime(&ms, a, b);
+        }
+        pir_multi_plan_destroy(plan);
+        if (rc != PIR_OK) break;
+        if (best_r == 0 || ms < best) {
+            best = ms;
+            best_r = (uint32_t)r;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != PIR_OK) return rc;
+    *best_item_log2 = best_r;
+    if (best_ms) *best_ms = best / 3.f;
+    return PIR_OK;
+}
+
+}  // extern "C"

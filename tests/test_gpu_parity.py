@@ -85,23 +85,8 @@ def test_fused_matches_oracle(env, rows, width, batch):
         assert np.array_equal(pir.pir_reconstruct(g0[q], g1[q]), want.astype(np.uint32))
 
 
-def _plans(pir, n, width):
-    out = []
-    for g in (1, 2, 4, 8):
-        lsq = {1: 8, 2: 7, 4: 6, 8: 5}[g]
-        for vec in (1, 4):
-            if vec == 4 and width % 4:
-                continue
-            for r in sorted({1, 2, 3, min(n, lsq), min(n, lsq + 1), min(n, lsq + 3), min(n, lsq + 9)}):
-                if r < 1 or r > n or r - min(lsq, r - 1) > 9:
-                    continue
-                if g * width > 2048:
-                    continue
-                out.append(pir.pir_plan(g, r, vec, 0))
-    return out
-
-
 def test_every_launch_shape_matches_oracle(env):
+    # every (group, load width, rows per item) the library accepts for this shape
     torch, pir, orc = env
     rows, width, batch = (1 << 13) + 333, 16, 9
     n = pir.pir_domain_bits(rows)
@@ -110,11 +95,19 @@ def test_every_launch_shape_matches_oracle(env):
     ks0, _ = make_keys(orc, n, alphas, [1] * batch, 77)
     want = np.stack([orc.answer(k, T) for k in ks0])
     table = dev_table(torch, T)
-    plans = _plans(pir, n, width)
-    assert len(plans) > 20
-    for plan in plans:
-        got = run_device(torch, pir, table, ks0, width, plan=plan)
-        assert np.array_equal(got, want), plan.as_dict()
+    ran = 0
+    for g in (1, 2, 4, 8):
+        for vec in (1, 4):
+            for r in range(1, n + 1):
+                plan = pir.pir_plan(g, r, vec, 0)
+                try:
+                    got = run_device(torch, pir, table, ks0, width, plan=plan)
+                except pir.PirError as e:
+                    assert e.code == -8, plan.as_dict()  # shape outside the kernels' limits
+                    continue
+                assert np.array_equal(got, want), plan.as_dict()
+                ran += 1
+    assert ran >= 80
 
 
 def test_host_entry_point_host_and_device_outputs(env):
