@@ -223,6 +223,70 @@ void pir_graph_destroy(pir_graph* graph);
 int pir_multi_autotune(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
                        const uint8_t* dkeys, uint32_t* dout, void* stream, uint32_t* best_item_log2, float* best_ms);
 
+/* ---- serving loop ---------------------------------------------------- */
+
+/* A server with resident tables that batches queries as they arrive
+ * (continuous cross-table batching).  The paper tunes a batch size per table
+ * offline (Sec. 3.2.1, Sec. 5 "batch size is tuned for each experiment");
+ * here the batch is whatever arrived while the previous batch ran.
+ * Requests are admitted into max_inflight slots (from a device-memory
+ * budget); a full pool refuses with PIR_ERR_BUSY.  A worker thread packs
+ * each batch's keys and work list into one pinned block and issues copy-in,
+ * the multi-table kernel and copy-out on one of `streams` CUDA streams, so a
+ * new batch overlaps the running one.  Results go straight into the
+ * caller's host buffer; latency runs from arrival to that copy. */
+typedef struct pir_server pir_server;
+
+typedef struct pir_server_config {
+    uint32_t max_batch;            /* queries per launch; 0 = 2048 */
+    uint32_t max_inflight;         /* admitted but unfinished queries; 0 = derived from the budget */
+    uint64_t device_memory_budget; /* bytes of key, share and work-list space behind max_inflight; 0 = 256 MiB */
+    uint32_t streams;              /* batches in flight at once, 1..8; 0 = 2 */
+    uint32_t item_log2;            /* rows per work item as a power of two; 0 = 15 */
+} pir_server_config;
+
+typedef struct pir_server_stats {
+    uint64_t submitted, completed, rejected, batches, batched_queries;
+    uint32_t max_inflight;
+} pir_server_stats;
+
+/* Starts the worker thread on the current device.  cfg may be NULL. */
+int pir_server_create(const pir_server_config* cfg, pir_server** server);
+
+/* Registers a resident table (device data, width <= 512 words); the server
+ * keeps the descriptor, the caller keeps the memory alive until destroy. */
+int pir_server_register_table(pir_server* server, const pir_table* t, uint32_t* table_id);
+
+/* Admits one query: key (host, pir_key_bytes(n) bytes, n of the table; copied
+ * before return) for table_id; its share (width words) is written to `out`
+ * (host) when done.  *ticket identifies it for pir_poll.  Errors:
+ * PIR_ERR_BUSY (pool full: retry later), PIR_ERR_KEY, PIR_ERR_DOMAIN,
+ * PIR_ERR_ARG. */
+int pir_submit(pir_server* server, uint32_t table_id, const uint8_t* key, uint32_t* out, uint64_t* ticket);
+
+/* PIR_OK when the ticket's share is in its buffer (the ticket is then
+ * released; *latency_ns = arrival to completion), PIR_ERR_BUSY while it is
+ * queued or running, PIR_ERR_ARG for an unknown ticket, or the error that
+ * failed its batch. */
+int pir_poll(pir_server* server, uint64_t ticket, int64_t* latency_ns);
+
+/* Waits until nothing is queued or running; PIR_ERR_TIMEOUT after timeout_ms. */
+int pir_server_drain(pir_server* server, uint32_t timeout_ms);
+
+int pir_server_stats_get(pir_server* server, pir_server_stats* stats);
+
+/* Open-loop load replay (measurement tool): submits query i at arrival_s[i]
+ * seconds after the call starts (a full pool delays the submission, and the
+ * latency still counts from the scheduled arrival), with keys at
+ * keys + key_offsets[i] and shares to outs + out_offsets[i] (host), then
+ * drains.  latency_ns[i] receives each latency; *elapsed_s the wall time. */
+int pir_server_replay(pir_server* server, const double* arrival_s, const uint32_t* table_ids, const uint8_t* keys,
+                      const uint64_t* key_offsets, size_t count, uint32_t* outs, const uint64_t* out_offsets,
+                      int64_t* latency_ns, double* elapsed_s);
+
+/* Drains, stops the worker and frees the server's buffers. */
+void pir_server_destroy(pir_server* server);
+
 /* ---- materialised (unfused) baseline ------------------------------- */
 
 #define PIR_CONTRACT_IMAD 0  /* CUDA-core 32-bit multiply-add */

@@ -37,6 +37,20 @@ class pir_table(ctypes.Structure):
                 ("stride", ctypes.c_uint64)]
 
 
+class pir_server_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("device_memory_budget", ctypes.c_uint64), ("streams", ctypes.c_uint32),
+                ("item_log2", ctypes.c_uint32)]
+
+
+class pir_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("batched_queries", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class pir_plan(ctypes.Structure):
     _fields_ = [("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32), ("vec", ctypes.c_uint32),
                 ("ctas", ctypes.c_uint32)]
@@ -81,6 +95,15 @@ def _load():
         "pir_multi_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, vp, ctypes.c_size_t, u8p,
                                               u32p, vp, ctypes.POINTER(ctypes.c_uint32),
                                               ctypes.POINTER(ctypes.c_float)]),
+        "pir_server_create": (ctypes.c_int, [ctypes.POINTER(pir_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+        "pir_server_register_table": (ctypes.c_int, [vp, ctypes.POINTER(pir_table), ctypes.POINTER(ctypes.c_uint32)]),
+        "pir_submit": (ctypes.c_int, [vp, ctypes.c_uint32, u8p, u32p, ctypes.POINTER(ctypes.c_uint64)]),
+        "pir_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
+        "pir_server_drain": (ctypes.c_int, [vp, ctypes.c_uint32]),
+        "pir_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(pir_server_stats)]),
+        "pir_server_replay": (ctypes.c_int, [vp, vp, vp, u8p, vp, ctypes.c_size_t, u32p, vp, vp,
+                                             ctypes.POINTER(ctypes.c_double)]),
+        "pir_server_destroy": (None, [vp]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
@@ -331,6 +354,77 @@ def pir_multi_autotune(tables, table_of_key, dkeys, dout, stream=None):
     _check(_lib.pir_multi_autotune(arr, len(tables), tk.ctypes.data, tk.size, dkeys.data_ptr(), dout.data_ptr(),
                                    _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "pir_multi_autotune")
     return best.value, ms.value
+
+
+class Server:
+    """Owner of a pir_server (continuous batching over resident tables)."""
+
+    def __init__(self, max_batch=0, max_inflight=0, device_memory_budget=0, streams=0, item_log2=0):
+        cfg = pir_server_config(max_batch, max_inflight, device_memory_budget, streams, item_log2)
+        h = ctypes.c_void_p()
+        _check(_lib.pir_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pir_server_create")
+        self.handle = h
+        self._tables = []
+
+    def register_table(self, table) -> int:
+        tid = ctypes.c_uint32()
+        _check(_lib.pir_server_register_table(self.handle, ctypes.byref(table_of(table)), ctypes.byref(tid)),
+               "pir_server_register_table")
+        self._tables.append(table)
+        return tid.value
+
+    def submit(self, table_id: int, key: bytes, out) -> int:
+        """`out`: host numpy uint32 array of the table's width (kept alive by the caller)."""
+        t = ctypes.c_uint64()
+        _check(_lib.pir_submit(self.handle, table_id, _buf(key), out.ctypes.data, ctypes.byref(t)), "pir_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else the latency in ns."""
+        lat = ctypes.c_int64()
+        rc = _lib.pir_poll(self.handle, ticket, ctypes.byref(lat))
+        if rc == -7:
+            return None
+        _check(rc, "pir_poll")
+        return lat.value
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(_lib.pir_server_drain(self.handle, timeout_ms), "pir_server_drain")
+
+    def stats(self) -> dict:
+        st = pir_server_stats()
+        _check(_lib.pir_server_stats_get(self.handle, ctypes.byref(st)), "pir_server_stats_get")
+        return st.as_dict()
+
+    def replay(self, arrival_s, table_ids, keys: bytes, key_offsets, outs, out_offsets):
+        """Open-loop replay; returns (latencies_ns array, elapsed seconds)."""
+        import numpy as np
+
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        tids = np.ascontiguousarray(table_ids, dtype=np.uint32)
+        koff = np.ascontiguousarray(key_offsets, dtype=np.uint64)
+        ooff = np.ascontiguousarray(out_offsets, dtype=np.uint64)
+        lat = np.zeros(arr.size, np.int64)
+        el = ctypes.c_double()
+        _check(_lib.pir_server_replay(self.handle, arr.ctypes.data, tids.ctypes.data, _buf(keys), koff.ctypes.data,
+                                      arr.size, outs.ctypes.data, ooff.ctypes.data, lat.ctypes.data,
+                                      ctypes.byref(el)), "pir_server_replay")
+        return lat, el.value
+
+    def close(self):
+        if self.handle:
+            _lib.pir_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pir_server_create(**cfg) -> Server:
+    return Server(**cfg)
 
 
 def pir_plan_for(rows: int, width: int, batch: int) -> pir_plan:

@@ -6,8 +6,8 @@
 //   P(0,0) = root;  P(d,j) = AES_{P(d-1,j>>1)}((j&1) || 0^120) ^ C_t[j&1][d],
 //   t = lsb(P(d-1,j>>1));  y(j) = (-1)^sigma (word1(P(n,j)) + lsb(P(n,j)) * cw_out).
 //
-// Structure.  One CTA of 512 threads per SM, persistent over work items; an
-// item is G queries x 2^r consecutive rows.
+// Structure.  One CTA per SM (512 producer + 128 consumer threads), persistent
+// over work items; an item is G queries x 2^r consecutive rows.
 //  1. lookup tables, built once per CTA: the S-box derived from GF(2^8), the
 //     four AES column tables Te0..Te3 (Te_r = rotl(Te0, 8r)), each with 32
 //     lane-private copies so that lane l always reads bank l.  A lookup is one
@@ -22,9 +22,12 @@
 //     PRF evaluation yields both children (one key schedule, two blocks that
 //     share their first two rounds' lookups); for leaves only the 5 output
 //     bytes that the share needs are computed in the last round.
-//  5. every kPairs leaf pairs the CTA stops and multiplies the fresh leaf
-//     shares of all G queries into register accumulators against the table
-//     rows they index, reading each row once for all G queries (Sec. 3.2.4).
+//  5. warp-specialised fusion (Sec. 3.2.4): 16 producer warps run steps 2-4
+//     and drop every kPairs leaf pairs' shares into one of two shared-memory
+//     buffers; 4 consumer warps multiply each buffer, for all G queries at
+//     once, into register accumulators against the table rows it indexes
+//     (each row read once per CTA), while the producers fill the other
+//     buffer.  Named barriers pass the buffers back and forth.
 //  6. accumulators are summed in shared memory and added to out with one
 //     u32 atomicAdd per (query, word); addition mod 2^32 is associative, so
 //     the result is bit-exact in any order.
@@ -38,16 +41,19 @@
 namespace pir {
 namespace dev {
 
-constexpr int kThreads = 512;
+constexpr int kProducers = 512;                             // threads that expand the tree
+constexpr int kConsumers = 128;                             // threads that multiply into the table
+constexpr int kFusedThreads = kProducers + kConsumers;
+constexpr int kMaxChunks = kConsumers;                      // W / VEC limit of the fused product
 constexpr int kPlaneBytes = 256 * 256;                     // 256 rows x [32 copies of Te_a | 32 of Te_b]
 constexpr int kTablesBytes = 2 * kPlaneBytes;              // plane 0: Te0|Te1, plane 1: Te2|Te3
 constexpr int kStackLevels = 8;                            // pending siblings per thread
 constexpr int kMaxDfsDepth = kStackLevels + 1;             // levels a thread expands on its own
 constexpr int kStackOff = kTablesBytes;
-constexpr int kStackBytes = kStackLevels * kThreads * 16;  // 64 KiB
+constexpr int kStackBytes = kStackLevels * kProducers * 16;  // 64 KiB
 constexpr int kPairs = 2;                                  // leaf pairs per subtree between MAC phases
 constexpr int kYOff = kStackOff + kStackBytes;
-constexpr int kYWords = 2 * 2 * kPairs * kThreads;         // two buffers of G x 2kPairs x SQ words
+constexpr int kYWords = 2 * 2 * kPairs * kProducers;       // two buffers of G x 2kPairs x SQ words
 constexpr int kHdrOff = kYOff + 4 * kYWords;
 constexpr int kMaxGroup = 8;
 constexpr int kHdrBytes = 32 * kMaxGroup;                  // per query: key ptr, out ptr, ok, party, cw_out
@@ -138,8 +144,7 @@ __device__ void build_tables(int tid) {
     __syncthreads();
     // 4 tables x 256 rows x 32 lane copies = 32768 words
 #pragma unroll 4
-    for (int i = 0; i < 32768 / kThreads; ++i) {
-        const int f = i * kThreads + tid;
+    for (int f = tid; f < 32768; f += (int)blockDim.x) {
         const int t = f >> 13, x = (f >> 5) & 255, lane = f & 31;
         const uint32_t v = stage[x];
         const uint32_t rv = t ? __funnelshift_l(v, v, 8 * t) : v;
@@ -217,15 +222,17 @@ __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x 
 // Children of v at depth d (1-based) of `key`: AES plus C_{lsb(v)}[b][d].
 __device__ __forceinline__ void expand(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
                                        bool leaf, uint4& c0, uint4& c1) {
-    prf2(lane4, lane4h, v, leaf, c0, c1);
+    // the codewords' address is known before the PRF: issue the loads first
     const uint4* cw = reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) + 32u * (v.x & 1u));
-    c0 = xor4(c0, __ldg(cw));
-    c1 = xor4(c1, __ldg(cw + 1));
+    const uint4 w0 = __ldg(cw), w1 = __ldg(cw + 1);
+    prf2(lane4, lane4h, v, leaf, c0, c1);
+    c0 = xor4(c0, w0);
+    c1 = xor4(c1, w1);
 }
 
 // Pending right sibling at relative level `lvl` (1..8) of thread `tid`.
 __device__ __forceinline__ uint4* stack_slot(int lvl, int tid) {
-    return reinterpret_cast<uint4*>(sm + kStackOff) + (lvl - 1) * kThreads + tid;
+    return reinterpret_cast<uint4*>(sm + kStackOff) + (lvl - 1) * kProducers + tid;
 }
 
 template <int VEC>
@@ -238,28 +245,57 @@ __device__ __forceinline__ void load_row(const uint32_t* p, uint32_t (&v)[VEC]) 
     }
 }
 
-// Multiply the shares of the last `kc` leaf pairs of every subtree into acc.
+// Named barriers between producers and consumers: kBarFull + b marks share
+// buffer b as filled, kBarFree + b as consumed (barrier 0 is __syncthreads).
+constexpr int kBarFull = 1, kBarFree = 3;
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Consumer thread `ct` of kConsumers: multiply the shares of leaf pairs
+// kbase..kbase+kc-1 of every subtree (buffer yb) into acc.  Consumer (c, rg)
+// owns words c*VEC..c*VEC+VEC-1 of every G query for rows rg, rg+nrg, ...;
+// four rows' loads are issued before their multiply-adds.
 template <int G, int VEC>
 __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* yb, uint64_t r0, int m, int sd,
-                                          uint32_t kbase, uint32_t kc, uint32_t (&acc)[G][VEC], int tid) {
-    constexpr int SQ = kThreads / G;
+                                          uint32_t kbase, uint32_t kc, uint32_t (&acc)[G][VEC], uint32_t ct) {
+    constexpr int SQ = kProducers / G;
     const uint32_t nc = p.width / VEC;
-    const uint32_t nrg = kThreads / nc;
-    const uint32_t c = (uint32_t)tid % nc, rg = (uint32_t)tid / nc;
+    const uint32_t nrg = kConsumers / nc;
+    const uint32_t c = ct % nc, rg = ct / nc;
     if (rg >= nrg) return;
     const uint32_t nrows = (2u * kc) << sd;
     const uint32_t submask = (1u << sd) - 1u;
-    for (uint32_t rr = rg; rr < nrows; rr += nrg) {
-        const uint32_t j = rr >> sd, l = rr & submask;
-        const uint64_t row = r0 + ((uint64_t)l << m) + 2ull * kbase + j;
-        if (row < p.row_lo || row >= p.row_hi) continue;
-        uint32_t tv[VEC];
-        load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv);
+    for (uint32_t rr0 = rg; rr0 < nrows; rr0 += 4 * nrg) {
+        uint32_t tv[4][VEC];
+        uint32_t yi[4];
+        bool ok[4];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const uint32_t y = yb[(g * 2 * kPairs + j) * SQ + l];
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t rr = rr0 + u * nrg;
+            const uint32_t j = rr >> sd, l = rr & submask;
+            const uint64_t row = r0 + ((uint64_t)l << m) + 2ull * kbase + j;
+            ok[u] = rr < nrows && row >= p.row_lo && row < p.row_hi;
+            yi[u] = j * SQ + l;
+            if (ok[u]) {
+                load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv[u]);
+            } else {
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) acc[g][i] += y * tv[i];
+                for (int i = 0; i < VEC; ++i) tv[u][i] = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const uint32_t y = yb[g * 2 * kPairs * SQ + yi[u]];
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) acc[g][i] += y * tv[u][i];
+            }
         }
     }
 }
@@ -269,7 +305,7 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
 template <int G>
 __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t* yb, uint32_t* dst, int g, int l,
                                             uint64_t row_base, uint32_t kc) {
-    constexpr int SQ = kThreads / G;
+    constexpr int SQ = kProducers / G;
     if (kc == 2 && p.shares_vec && row_base >= p.row_lo && row_base + 4 <= p.row_hi &&
         ((row_base - p.row_lo) & 3u) == 0) {
         uint4 v;
@@ -287,17 +323,20 @@ __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t
 }
 
 // One work item: the queries in the header slots (set by the caller) over the
-// 2^r rows starting at r0.  MAT = false: fused share x table product (a1-a6);
-// MAT = true: expansion only, leaf shares written to each slot's `out`.
+// 2^r rows starting at r0.  MAT = false: fused share x table product (a1-a6)
+// with kConsumers consumer threads after the kProducers producers;
+// MAT = true: producers only, leaf shares written to each slot's `out`.
 // Ends with a barrier, so shared memory is free for the next item.
 template <int G, int VEC, bool MAT>
 __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
-    constexpr int SQ = kThreads / G;
+    constexpr int SQ = kProducers / G;
     constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
+    constexpr int NT = MAT ? kProducers : kFusedThreads;
     static_assert(G * 2 * kPairs * SQ * 2 <= kYWords, "share buffers exceed their region");
     static_assert(G <= kMaxGroup, "too many query slots");
 
     const int tid = threadIdx.x;
+    const bool producer = tid < kProducers;
     const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
     uint32_t* ybuf = reinterpret_cast<uint32_t*>(sm + kYOff);
     const int n = (int)p.n, r = (int)p.range_log2;
@@ -306,7 +345,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
 
     // ---- key headers and the path to this item's range node ---------------
     uint4* bufA = reinterpret_cast<uint4*>(ybuf);
-    uint4* bufB = bufA + kThreads;
+    uint4* bufB = bufA + kProducers;
     if (tid < G) {
         QueryHdr* h = hdr_slot(tid);
         uint32_t ok = 0, party = 0, cwo = 0;
@@ -337,7 +376,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     }
     __syncthreads();
 
-    // ---- split to one subtree root per thread ------------------------------
+    // ---- split to one subtree root per producer thread ----------------------
     for (int i = 0; i < sd; ++i) {
         const uint4* src = (i & 1) ? bufB : bufA;
         uint4* dst = (i & 1) ? bufA : bufB;
@@ -352,78 +391,93 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         }
         __syncthreads();
     }
-    const int g = tid / SQ, l = tid % SQ;
     const int nsub = 1 << sd;
+    const uint32_t npairs = 1u << (m - 1);
+    const uint32_t kc = npairs < (uint32_t)kPairs ? npairs : (uint32_t)kPairs;
+    const uint32_t nphases = npairs / kc;
+    const int g = producer ? tid / SQ : 0, l = producer ? tid % SQ : 0;
     const QueryHdr* hq = hdr_slot(g);
-    const bool act = l < nsub && hq->ok != 0;
-    const uint32_t party = hq->party, cwo = hq->cw_out;
-    const uint8_t* key = hq->key;
+    const bool act = producer && l < nsub && hq->ok != 0;
     uint4 node = make_uint4(0, 0, 0, 0);
-    if (l < nsub) node = ((sd & 1) ? bufB : bufA)[(g << sd) + l];
+    if (producer && l < nsub) node = ((sd & 1) ? bufB : bufA)[(g << sd) + l];
     __syncthreads();  // share buffers alias the split buffers
 
-    // ---- depth-first expansion with periodic table products ----------------
     uint32_t acc[G][VEC];
 #pragma unroll
     for (int a = 0; a < G; ++a)
 #pragma unroll
         for (int i = 0; i < VEC; ++i) acc[a][i] = 0;
 
-    const int d0 = n - r + sd;  // depth of this thread's subtree root
-    const uint32_t npairs = 1u << (m - 1);
-    const uint32_t kc = npairs < (uint32_t)kPairs ? npairs : (uint32_t)kPairs;
-    int lvl = 0;
-    uint32_t k = 0, phase = 0;
-    for (;;) {
-        const bool leaf = lvl + 1 == m;
-        uint4 c0 = node, c1 = node;
-        if (act) expand(lane4, lane4h, key, (uint32_t)(d0 + lvl + 1), node, leaf, c0, c1);
-        if (leaf) {
-            uint32_t y0 = 0, y1 = 0;
-            if (act) {
-                y0 = c0.y + (c0.x & 1u) * cwo;
-                y1 = c1.y + (c1.x & 1u) * cwo;
-                if (party) {
-                    y0 = 0u - y0;
-                    y1 = 0u - y1;
+    if (producer) {
+        // ---- depth-first expansion; hand over shares every kc leaf pairs ----
+        const uint32_t party = hq->party, cwo = hq->cw_out;
+        const uint8_t* key = hq->key;
+        const int d0 = n - r + sd;  // depth of this thread's subtree root
+        int lvl = 0;
+        uint32_t k = 0, phase = 0;
+        for (;;) {
+            const bool leaf = lvl + 1 == m;
+            uint4 c0 = node, c1 = node;
+            if (act) expand(lane4, lane4h, key, (uint32_t)(d0 + lvl + 1), node, leaf, c0, c1);
+            if (leaf) {
+                uint32_t y0 = 0, y1 = 0;
+                if (act) {
+                    y0 = c0.y + (c0.x & 1u) * cwo;
+                    y1 = c1.y + (c1.x & 1u) * cwo;
+                    if (party) {
+                        y0 = 0u - y0;
+                        y1 = 0u - y1;
+                    }
                 }
-            }
-            uint32_t* yb = ybuf + (phase & 1u) * (kYWords / 2);
-            const uint32_t j = 2u * (k % kc);
-            yb[(g * 2 * kPairs + j) * SQ + l] = y0;
-            yb[(g * 2 * kPairs + j + 1) * SQ + l] = y1;
-            ++k;
-            if (k % kc == 0) {
-                if constexpr (MAT) {
-                    // each thread stores only what it wrote itself: no barrier needed
-                    if (hq->out && l < nsub)
-                        store_phase<G>(p, yb, hq->out, g, l, r0 + ((uint64_t)l << m) + 2ull * (k - kc), kc);
-                } else {
-                    __syncthreads();
-                    mac_phase<G, VEC>(p, yb, r0, m, sd, k - kc, kc, acc, tid);
+                uint32_t* yb = ybuf + (phase & 1u) * (kYWords / 2);
+                const uint32_t j = 2u * (k % kc);
+                yb[(g * 2 * kPairs + j) * SQ + l] = y0;
+                yb[(g * 2 * kPairs + j + 1) * SQ + l] = y1;
+                ++k;
+                if (k % kc == 0) {
+                    if constexpr (MAT) {
+                        // each thread stores only what it wrote itself: no barrier needed
+                        if (hq->out && l < nsub)
+                            store_phase<G>(p, yb, hq->out, g, l, r0 + ((uint64_t)l << m) + 2ull * (k - kc), kc);
+                    } else {
+                        bar_arrive(kBarFull + (int)(phase & 1u), kFusedThreads);
+                    }
+                    ++phase;
+                    if constexpr (!MAT) {
+                        // the next buffer was filled two phases ago: wait until it is consumed
+                        if (phase >= 2 && phase < nphases) bar_sync(kBarFree + (int)(phase & 1u), kFusedThreads);
+                    }
                 }
-                ++phase;
+                if (k == npairs) break;
+                lvl = m - 1 - (__ffs((int)k) - 1);
+                node = *stack_slot(lvl, tid);
+            } else {
+                *stack_slot(lvl + 1, tid) = c1;
+                node = c0;
+                ++lvl;
             }
-            if (k == npairs) break;
-            lvl = m - 1 - (__ffs((int)k) - 1);
-            node = *stack_slot(lvl, tid);
-        } else {
-            *stack_slot(lvl + 1, tid) = c1;
-            node = c0;
-            ++lvl;
+        }
+    } else if constexpr (!MAT) {
+        // ---- consumers: multiply every filled buffer into the accumulators ----
+        const uint32_t ct = (uint32_t)(tid - kProducers);
+        for (uint32_t ph = 0; ph < nphases; ++ph) {
+            bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
+            mac_phase<G, VEC>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
+            if (ph + 2 < nphases) bar_arrive(kBarFree + (int)(ph & 1u), kFusedThreads);
         }
     }
 
     __syncthreads();
     if constexpr (MAT) return;
-    // ---- reduce the per-thread partial sums, then one atomic per word ------
+    // ---- reduce the consumers' partial sums, then one atomic per word -------
     const uint32_t W = p.width;
     uint32_t* red = ybuf;
-    for (uint32_t i = tid; i < G * W; i += kThreads) red[i] = 0;
+    for (uint32_t i = tid; i < G * W; i += NT) red[i] = 0;
     __syncthreads();
-    {
-        const uint32_t nc = W / VEC, nrg = kThreads / nc;
-        const uint32_t c = (uint32_t)tid % nc, rg = (uint32_t)tid / nc;
+    if (!producer) {
+        const uint32_t ct = (uint32_t)(tid - kProducers);
+        const uint32_t nc = W / VEC, nrg = kConsumers / nc;
+        const uint32_t c = ct % nc, rg = ct / nc;
         if (rg < nrg) {
 #pragma unroll
             for (int a = 0; a < G; ++a)
@@ -433,7 +487,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         }
     }
     __syncthreads();
-    for (uint32_t i = tid; i < G * W; i += kThreads) {
+    for (uint32_t i = tid; i < G * W; i += NT) {
         const uint32_t a = i / W;
         const uint32_t v = red[i];
         uint32_t* o = hdr_slot((int)a)->out;
@@ -466,12 +520,12 @@ __device__ __forceinline__ void eval_items(const FusedParams& p) {
 }
 
 template <int G, int VEC>
-__global__ void __launch_bounds__(kThreads, 1) fused_eval_kernel(const FusedParams p) {
+__global__ void __launch_bounds__(kFusedThreads, 1) fused_eval_kernel(const FusedParams p) {
     eval_items<G, VEC, false>(p);
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads, 1) expand_materialise_kernel(const FusedParams p) {
+__global__ void __launch_bounds__(kProducers, 1) expand_materialise_kernel(const FusedParams p) {
     eval_items<G, 1, true>(p);
 }
 
@@ -479,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) expand_materialise_kernel(const F
 // (table, row range, up to 8 queries of that table); CTAs take the next item
 // from a counter, so uneven items balance themselves.
 template <int VEC>
-__global__ void __launch_bounds__(kThreads, 1) multi_eval_kernel(const MultiParams mp) {
+__global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const MultiParams mp) {
     build_tables(threadIdx.x);
     uint64_t* s_item = reinterpret_cast<uint64_t*>(sm + kItemOff);
     for (;;) {
@@ -511,11 +565,11 @@ __global__ void __launch_bounds__(kThreads, 1) multi_eval_kernel(const MultiPara
 }
 
 template <typename Kern>
-cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, cudaStream_t s) {
+cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, int threads, cudaStream_t s) {
     // the attribute is per function and device; setting it each launch costs ~1 us and is always correct
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    kern<<<ctas, kThreads, kSmemBytes, s>>>(p);
+    kern<<<ctas, threads, kSmemBytes, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -531,7 +585,7 @@ int device_sm_count() {
 }
 
 static int log_sq(uint32_t group) {
-    const int sq = dev::kThreads / (int)group;
+    const int sq = dev::kProducers / (int)group;
     int l = 0;
     while ((1 << l) < sq) ++l;
     return l;
@@ -547,7 +601,7 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     if (plan.group != 1 && plan.group != 2 && plan.group != 4 && plan.group != 8) return PIR_ERR_UNSUPPORTED;
     if (plan.vec != 1 && plan.vec != 4) return PIR_ERR_UNSUPPORTED;
     if (plan.vec == 4 && (!vec_ok || width % 4 != 0)) return PIR_ERR_UNSUPPORTED;
-    if (width == 0 || width / plan.vec > (uint32_t)dev::kThreads) return PIR_ERR_UNSUPPORTED;
+    if (width == 0 || width / plan.vec > (uint32_t)dev::kMaxChunks) return PIR_ERR_UNSUPPORTED;
     if ((uint64_t)plan.group * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
     const int r = (int)plan.range_log2;
     if (r < 1 || r > (int)n) return PIR_ERR_UNSUPPORTED;
@@ -561,7 +615,7 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     if (width == 0 || batch == 0 || n == 0) return PIR_ERR_ARG;
     pir_plan pl{};
     pl.vec = (vec_ok && width % 4 == 0) ? 4 : 1;
-    if (width / pl.vec > (uint32_t)dev::kThreads) return PIR_ERR_UNSUPPORTED;
+    if (width / pl.vec > (uint32_t)dev::kMaxChunks) return PIR_ERR_UNSUPPORTED;
     uint32_t g = 8;
     while (g > 1 && (g > batch || (uint64_t)g * width > (uint64_t)dev::kYWords)) g >>= 1;
     if ((uint64_t)g * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
@@ -616,10 +670,10 @@ int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* s
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
     switch (plan.group) {
-        case 1: e = dev::launch_kernel(dev::expand_materialise_kernel<1>, p, ctas, s); break;
-        case 2: e = dev::launch_kernel(dev::expand_materialise_kernel<2>, p, ctas, s); break;
-        case 4: e = dev::launch_kernel(dev::expand_materialise_kernel<4>, p, ctas, s); break;
-        default: e = dev::launch_kernel(dev::expand_materialise_kernel<8>, p, ctas, s); break;
+        case 1: e = dev::launch_kernel(dev::expand_materialise_kernel<1>, p, ctas, dev::kProducers, s); break;
+        case 2: e = dev::launch_kernel(dev::expand_materialise_kernel<2>, p, ctas, dev::kProducers, s); break;
+        case 4: e = dev::launch_kernel(dev::expand_materialise_kernel<4>, p, ctas, dev::kProducers, s); break;
+        default: e = dev::launch_kernel(dev::expand_materialise_kernel<8>, p, ctas, dev::kProducers, s); break;
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "expand_materialise launch");
 }
@@ -634,7 +688,7 @@ int launch_multi(const MultiParams& mp, bool vec, void* stream) {
     auto kern = vec ? dev::multi_eval_kernel<4> : dev::multi_eval_kernel<1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kSmemBytes);
     if (e == cudaSuccess) {
-        kern<<<ctas, dev::kThreads, dev::kSmemBytes, s>>>(mp);
+        kern<<<ctas, dev::kFusedThreads, dev::kSmemBytes, s>>>(mp);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "multi_eval launch");
@@ -648,17 +702,17 @@ int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
     cudaError_t e = cudaSuccess;
     if (plan.vec == 4) {
         switch (plan.group) {
-            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 4>, p, ctas, s); break;
-            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 4>, p, ctas, s); break;
-            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 4>, p, ctas, s); break;
-            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 4>, p, ctas, s); break;
+            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 4>, p, ctas, dev::kFusedThreads, s); break;
+            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 4>, p, ctas, dev::kFusedThreads, s); break;
+            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 4>, p, ctas, dev::kFusedThreads, s); break;
+            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 4>, p, ctas, dev::kFusedThreads, s); break;
         }
     } else {
         switch (plan.group) {
-            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 1>, p, ctas, s); break;
-            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 1>, p, ctas, s); break;
-            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 1>, p, ctas, s); break;
-            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 1>, p, ctas, s); break;
+            case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 1>, p, ctas, dev::kFusedThreads, s); break;
+            case 2: e = dev::launch_kernel(dev::fused_eval_kernel<2, 1>, p, ctas, dev::kFusedThreads, s); break;
+            case 4: e = dev::launch_kernel(dev::fused_eval_kernel<4, 1>, p, ctas, dev::kFusedThreads, s); break;
+            default: e = dev::launch_kernel(dev::fused_eval_kernel<8, 1>, p, ctas, dev::kFusedThreads, s); break;
         }
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "fused_eval launch");

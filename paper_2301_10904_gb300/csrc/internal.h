@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "pir.h"
 
@@ -67,6 +68,19 @@ struct MultiParams {
     uint64_t* counter;  // next item; zeroed before each launch
 };
 int launch_multi(const MultiParams& mp, bool vec, void* stream);
+
+// Host side of the multi-table planner (multi.cpp): fills `mt` from the
+// descriptors and appends the work items; offsets of keys (bytes) and shares
+// (words) in query order.  Returns PIR_OK or an error code.
+struct MultiLayout {
+    std::vector<MultiTable> tables;
+    std::vector<MultiItem> items;
+    std::vector<uint64_t> key_off, out_off;
+    uint64_t key_total = 0, out_total = 0;
+    bool vec = true;
+};
+int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2, MultiLayout& lay);
+int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay);
 int multi_group();          // queries per item
 int multi_max_range_log2(); // largest rows-per-item exponent the kernel supports
 

@@ -67,6 +67,74 @@ int upload(T** dst, const std::vector<T>& src) {
 }
 
 }  // namespace
+
+int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2, MultiLayout& lay) {
+    const int G = multi_group();
+    const int rmax = multi_max_range_log2();
+    if (item_log2 == 0) item_log2 = (uint32_t)rmax;
+    if ((int)item_log2 > rmax) return PIR_ERR_UNSUPPORTED;
+    lay.tables.assign(ntables, MultiTable{});
+    lay.vec = true;
+    for (size_t t = 0; t < ntables; ++t) {
+        const pir_table& tb = tables[t];
+        if (!tb.data || tb.rows < 1 || tb.width < 1 || tb.stride < tb.width ||
+            (reinterpret_cast<uintptr_t>(tb.data) & 3u) != 0)
+            return PIR_ERR_ARG;
+        if ((uint64_t)G * tb.width > 4096u) return PIR_ERR_UNSUPPORTED;
+        const uint32_t n = pir_domain_bits(tb.rows);
+        if (n == 0) return PIR_ERR_DOMAIN;
+        lay.vec = lay.vec && (reinterpret_cast<uintptr_t>(tb.data) & 15u) == 0 && tb.stride % 4 == 0 &&
+                  tb.width % 4 == 0;
+        MultiTable& m = lay.tables[t];
+        m.data = tb.data;
+        m.rows = tb.rows;
+        m.stride = tb.stride;
+        m.width = tb.width;
+        m.n = n;
+        m.key_bytes = (uint32_t)key_bytes(n);
+        m.range_log2 = std::min<uint32_t>(n, item_log2);
+    }
+    return PIR_OK;
+}
+
+int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay) {
+    const int G = multi_group();
+    const size_t ntables = lay.tables.size();
+    lay.key_off.resize(batch);
+    lay.out_off.resize(batch);
+    lay.key_total = lay.out_total = 0;
+    lay.items.clear();
+    std::vector<std::vector<uint32_t>> per_table(ntables);
+    for (size_t q = 0; q < batch; ++q) {
+        const uint32_t t = table_of_key[q];
+        if (t >= ntables) return PIR_ERR_ARG;
+        lay.key_off[q] = lay.key_total;
+        lay.out_off[q] = lay.out_total;
+        lay.key_total += lay.tables[t].key_bytes;
+        lay.out_total += lay.tables[t].width;
+        per_table[t].push_back((uint32_t)q);
+    }
+    for (size_t t = 0; t < ntables; ++t) {
+        const auto& qs = per_table[t];
+        if (qs.empty()) continue;
+        const uint64_t ranges = ((lay.tables[t].rows - 1) >> lay.tables[t].range_log2) + 1;
+        const size_t groups = (qs.size() + G - 1) / G;
+        for (uint64_t rg = 0; rg < ranges; ++rg) {
+            for (size_t gi = 0; gi < groups; ++gi) {
+                MultiItem it{};
+                it.table = (uint32_t)t;
+                it.range = rg;
+                for (int s = 0; s < 8; ++s) {
+                    const size_t idx = gi * G + s;
+                    it.q[s] = (s < G && idx < qs.size()) ? qs[idx] : kNoQuery;
+                }
+                lay.items.push_back(it);
+            }
+        }
+    }
+    return PIR_OK;
+}
+
 }  // namespace pir
 
 extern "C" {
@@ -78,82 +146,23 @@ int pir_multi_plan_create(const pir_table* tables, size_t ntables, const uint32_
         !out_plan)
         return PIR_ERR_ARG;
     *out_plan = nullptr;
-    const int G = multi_group();
-    const int rmax = multi_max_range_log2();
-    if (item_log2 == 0) item_log2 = (uint32_t)rmax;
-    if ((int)item_log2 > rmax) return PIR_ERR_UNSUPPORTED;
-
+    MultiLayout lay;
+    int rc = describe_tables(tables, ntables, item_log2, lay);
+    if (rc == PIR_OK) rc = plan_items(table_of_key, batch, lay);
+    if (rc != PIR_OK) return rc;
     pir_multi_plan* plan = new (std::nothrow) pir_multi_plan();
     if (!plan) return PIR_ERR_NOMEM;
     plan->batch = (uint32_t)batch;
     plan->item_log2 = item_log2;
+    plan->vec = lay.vec;
     cudaGetDevice(&plan->device);
-
-    std::vector<MultiTable> mt(ntables);
-    for (size_t t = 0; t < ntables; ++t) {
-        const pir_table& tb = tables[t];
-        if (!tb.data || tb.rows < 1 || tb.width < 1 || tb.stride < tb.width ||
-            (reinterpret_cast<uintptr_t>(tb.data) & 3u) != 0) {
-            free_plan(plan);
-            return PIR_ERR_ARG;
-        }
-        if ((uint64_t)G * tb.width > 4096u || tb.width > 512u) {
-            free_plan(plan);
-            return PIR_ERR_UNSUPPORTED;
-        }
-        const uint32_t n = pir_domain_bits(tb.rows);
-        if (n == 0) {
-            free_plan(plan);
-            return PIR_ERR_DOMAIN;
-        }
-        plan->vec = plan->vec && (reinterpret_cast<uintptr_t>(tb.data) & 15u) == 0 && tb.stride % 4 == 0 &&
-                    tb.width % 4 == 0;
-        mt[t].data = tb.data;
-        mt[t].rows = tb.rows;
-        mt[t].stride = tb.stride;
-        mt[t].width = tb.width;
-        mt[t].n = n;
-        mt[t].key_bytes = (uint32_t)key_bytes(n);
-        mt[t].range_log2 = std::min<uint32_t>(n, item_log2);
-    }
-    // offsets of keys and shares in query order; queries grouped per table
-    plan->key_off.resize(batch);
-    plan->out_off.resize(batch);
-    std::vector<std::vector<uint32_t>> per_table(ntables);
-    for (size_t q = 0; q < batch; ++q) {
-        const uint32_t t = table_of_key[q];
-        if (t >= ntables) {
-            free_plan(plan);
-            return PIR_ERR_ARG;
-        }
-        plan->key_off[q] = plan->key_total;
-        plan->out_off[q] = plan->out_total;
-        plan->key_total += mt[t].key_bytes;
-        plan->out_total += mt[t].width;
-        per_table[t].push_back((uint32_t)q);
-    }
-    std::vector<MultiItem> items;
-    for (size_t t = 0; t < ntables; ++t) {
-        const auto& qs = per_table[t];
-        if (qs.empty()) continue;
-        const uint64_t ranges = ((mt[t].rows - 1) >> mt[t].range_log2) + 1;
-        const size_t groups = (qs.size() + G - 1) / G;
-        for (uint64_t rg = 0; rg < ranges; ++rg) {
-            for (size_t gi = 0; gi < groups; ++gi) {
-                MultiItem it{};
-                it.table = (uint32_t)t;
-                it.range = rg;
-                for (int s = 0; s < 8; ++s) {
-                    const size_t idx = gi * G + s;
-                    it.q[s] = (s < G && idx < qs.size()) ? qs[idx] : kNoQuery;
-                }
-                items.push_back(it);
-            }
-        }
-    }
-    plan->nitems = items.size();
-    int rc = upload(&plan->d_tables, mt);
-    if (rc == PIR_OK) rc = upload(&plan->d_items, items);
+    plan->key_off = std::move(lay.key_off);
+    plan->out_off = std::move(lay.out_off);
+    plan->key_total = lay.key_total;
+    plan->out_total = lay.out_total;
+    plan->nitems = lay.items.size();
+    rc = upload(&plan->d_tables, lay.tables);
+    if (rc == PIR_OK) rc = upload(&plan->d_items, lay.items);
     if (rc == PIR_OK) rc = upload(&plan->d_key_off, plan->key_off);
     if (rc == PIR_OK) rc = upload(&plan->d_out_off, plan->out_off);
     if (rc == PIR_OK) {
