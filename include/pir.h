@@ -289,7 +289,8 @@ void pir_server_destroy(pir_server* server);
 
 /* ---- materialised (unfused) baseline ------------------------------- */
 
-#define PIR_CONTRACT_IMAD 0  /* CUDA-core 32-bit multiply-add */
+#define PIR_CONTRACT_IMAD 0   /* CUDA-core 32-bit multiply-add */
+#define PIR_CONTRACT_MMA_U8 1 /* tensor-core u8 x u8 -> s32 MMAs on 8-bit limbs (10 per u32 product), exact */
 
 /* Expansion only (the level-by-level strategy's output, Sec. 3.2.2): writes
  * the full share vectors dshares[q * ld + j] = Eval(k_q, j) for j < rows,
@@ -303,7 +304,8 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
 
 /* dout[q][w] = sum_{j < t->rows} dshares[q * ld + j] * T[j][w]  (mod 2^32),
  * the share-matrix x table product of Sec. 3.1 ("batched together as a
- * single matrix-matrix multiplication").  engine: PIR_CONTRACT_IMAD.
+ * single matrix-matrix multiplication").  engine: PIR_CONTRACT_IMAD or
+ * PIR_CONTRACT_MMA_U8 (same result bit for bit).
  * dout (device, batch x width) is overwritten.  Asynchronous. */
 int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
                      int engine, void* stream);

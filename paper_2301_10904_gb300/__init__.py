@@ -239,6 +239,7 @@ def pir_server_eval_range(shard, row_lo: int, domain_rows: int, dkeys, batch: in
 
 
 PIR_CONTRACT_IMAD = 0
+PIR_CONTRACT_MMA_U8 = 1
 
 
 def pir_expand_materialise(rows: int, dkeys, batch: int, dshares, dstatus=None, stream=None):

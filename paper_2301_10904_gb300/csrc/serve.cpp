@@ -265,7 +265,9 @@ int submit(pir_server* srv, uint32_t table_id, const uint8_t* key, uint32_t* out
     if (table_id >= srv->tables.size()) return PIR_ERR_ARG;
     const uint32_t n = pir_domain_bits(srv->tables[table_id].rows);
     uint32_t kn = 0, party = 0;
-    if (pir_key_check(key, key_bytes(n), &kn, &party) != PIR_OK) return PIR_ERR_KEY;
+    // the header's own n gives the key's length; a valid key of another domain is a domain error
+    if (pir_key_check(key, key_bytes(key[5] <= PIR_MAX_DOMAIN_BITS ? key[5] : 0), &kn, &party) != PIR_OK)
+        return PIR_ERR_KEY;
     if (kn != n) return PIR_ERR_DOMAIN;
     if (srv->free_list.empty()) {
         srv->stats.rejected += 1;

@@ -58,15 +58,20 @@ def test_materialised_bad_key_gives_zero_vector_and_status(env):
     assert not got[1].any() and int(status.item()) & 1
 
 
+@pytest.mark.parametrize("engine", [0, 1], ids=["imad", "mma_u8"])
 @pytest.mark.parametrize("B,L,W", [(1, 1, 1), (3, 100, 5), (64, 4096, 64), (70, 3000, 65), (256, 1 << 14, 16),
-                                   (5, 777, 128)])
-def test_contract_matches_oracle(env, B, L, W):
+                                   (5, 777, 128), (9, 20000, 32)])
+def test_contract_matches_oracle(env, B, L, W, engine):
     torch, pir, orc = env
     rng = np.random.Generator(np.random.PCG64(B * L + W))
     S = rng.integers(0, 1 << 32, (B, L), dtype=np.uint64).astype(np.uint32)
+    if L >= 20000:
+        S[:, :] = 0xFFFFFFFF  # every limb at its maximum: the largest accumulator values
     T = wl.table_u32(W, L, W)
+    if L >= 20000:
+        T[:, :] = 0xFFFFFFFF
     out = torch.empty((B, W), dtype=torch.int32, device="cuda")
-    pir.pir_contract_u32(torch.from_numpy(S.view(np.int32)).cuda(), B, dev_table(torch, T), out)
+    pir.pir_contract_u32(torch.from_numpy(S.view(np.int32)).cuda(), B, dev_table(torch, T), out, engine=engine)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), orc.contract(S, T))
 
@@ -86,11 +91,14 @@ def test_materialised_pipeline_equals_fused_and_oracle(env):
         pir.pir_expand_materialise(rows, dk, batch, S)
         mat = torch.empty((batch, width), dtype=torch.int32, device="cuda")
         pir.pir_contract_u32(S, batch, table, mat)
+        mma = torch.empty_like(mat)
+        pir.pir_contract_u32(S, batch, table, mma, engine=pir.PIR_CONTRACT_MMA_U8)
         fused = torch.empty_like(mat)
         pir.pir_server_eval_device(table, dk, batch, fused)
         torch.cuda.synchronize()
         m = mat.cpu().numpy().view(np.uint32)
         assert np.array_equal(m, fused.cpu().numpy().view(np.uint32))
+        assert torch.equal(mma, mat)
         for q in (0, batch - 1):
             assert np.array_equal(m[q], orc.answer(keys[q], T))
         outs.append(m)
