@@ -314,6 +314,17 @@ int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const p
  * device (heuristic, or the autotuned entry when one is cached). */
 int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
 
+/* Autotuner of the fused path's launch shape (the paper tunes batch and
+ * strategy per table size, Sec. 3.2.1 and 3.2.5): times the fused kernel on
+ * this table and batch (device keys dkeys, device shares dout; synchronizes
+ * `stream`) for query groups G in {8,4,2,1} and rows per item 2^r around the
+ * heuristic's choice, and remembers the fastest for (device, rows, width,
+ * batch rounded up to a power of two); pir_server_eval*, pir_plan_for and
+ * pir_server_eval_noalloc use it from then on.  Returns it in *plan and its
+ * time per launch in *best_ms (optional). */
+int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
+                 pir_plan* plan, float* best_ms);
+
 /* Human-readable name of an error code (static string). */
 const char* pir_error_string(int code);
 

@@ -104,6 +104,8 @@ def _load():
         "pir_server_replay": (ctypes.c_int, [vp, vp, vp, u8p, vp, ctypes.c_size_t, u32p, vp, vp,
                                              ctypes.POINTER(ctypes.c_double)]),
         "pir_server_destroy": (None, [vp]),
+        "pir_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp,
+                                        ctypes.POINTER(pir_plan), ctypes.POINTER(ctypes.c_float)]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
@@ -426,6 +428,15 @@ class Server:
 
 def pir_server_create(**cfg) -> Server:
     return Server(**cfg)
+
+
+def pir_autotune(table, dkeys, batch: int, dout, stream=None):
+    """Times launch shapes on this batch; returns (pir_plan, ms per launch).
+    The library keeps using the winner for this table shape and batch size."""
+    plan, ms = pir_plan(), ctypes.c_float()
+    _check(_lib.pir_autotune(ctypes.byref(table_of(table)), dkeys.data_ptr(), batch, dout.data_ptr(),
+                             _stream(stream), ctypes.byref(plan), ctypes.byref(ms)), "pir_autotune")
+    return plan, ms.value
 
 
 def pir_plan_for(rows: int, width: int, batch: int) -> pir_plan:

@@ -3,6 +3,8 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -40,6 +42,42 @@ static bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ---- autotuned launch shapes --------------------------------------------
+// Keyed by (device, rows, width, batch rounded up to a power of two, whether
+// 128-bit loads apply); filled by pir_autotune, read by every evaluation.
+struct ShapeKey {
+    int device;
+    uint64_t rows;
+    uint32_t width;
+    uint32_t batch_bucket;
+    bool vec;
+    bool operator<(const ShapeKey& o) const {
+        if (device != o.device) return device < o.device;
+        if (rows != o.rows) return rows < o.rows;
+        if (width != o.width) return width < o.width;
+        if (batch_bucket != o.batch_bucket) return batch_bucket < o.batch_bucket;
+        return vec < o.vec;
+    }
+};
+static std::mutex g_tuned_mu;
+static std::map<ShapeKey, pir_plan> g_tuned;
+
+static ShapeKey shape_key(uint64_t rows, uint32_t width, size_t batch, bool vec) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint32_t bucket = 1;
+    while (bucket < batch && bucket < (1u << 30)) bucket <<= 1;
+    return ShapeKey{dev, rows, width, bucket, vec};
+}
+
+static bool tuned_plan(uint64_t rows, uint32_t width, size_t batch, bool vec, pir_plan* out) {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    auto it = g_tuned.find(shape_key(rows, width, batch, vec));
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 // Runs the fused evaluation of rows [row_lo, row_lo + shard->rows) of a
 // 2^n-leaf domain for device keys into a zeroed device output.
 static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
@@ -54,7 +92,8 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
         plan = *plan_in;
         int rc = plan_check(plan, n, shard->width, v);
         if (rc != PIR_OK) return rc;
-    } else {
+    } else if (row_lo != 0 || !tuned_plan(shard->rows, shard->width, batch, v, &plan) ||
+               plan_check(plan, n, shard->width, v) != PIR_OK) {
         int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
         if (rc != PIR_OK) return rc;
     }
@@ -99,7 +138,71 @@ int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan) {
     if (!plan || rows < 1 || width == 0 || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
     const uint32_t n = pir_domain_bits(rows);
     if (n == 0) return PIR_ERR_DOMAIN;
+    if (pir::tuned_plan(rows, width, batch, width % 4 == 0, plan)) return PIR_OK;
     return pir::plan_fused(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, plan);
+}
+
+int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
+                 pir_plan* best_plan, float* best_ms) {
+    using namespace pir;
+    if (!table_ok(t) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu || !best_plan) return PIR_ERR_ARG;
+    const uint32_t n = pir_domain_bits(t->rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    const bool v = vec_ok(t);
+    pir_plan base{};
+    int rc = plan_fused(t->rows, 0, n, t->width, (uint32_t)batch, v, &base);
+    if (rc != PIR_OK) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    pir_plan best = base;
+    float best_t = -1.f;
+    for (uint32_t g = 8; g >= 1; g >>= 1) {
+        if (g > batch || (uint64_t)g * t->width > 4096u) continue;
+        for (int r = (int)n; r >= 1; --r) {
+            pir_plan pl{g, (uint32_t)r, base.vec, 0};
+            if (plan_check(pl, n, t->width, v) != PIR_OK) continue;
+            // keep shapes with at least one item per SM, or the whole table in one item
+            const uint32_t nqg = (uint32_t)((batch + g - 1) / g);
+            const uint64_t items = (((t->rows - 1) >> r) + 1) * nqg;
+            if (items < (uint64_t)std::max(1, device_sm_count()) / 2 && r != (int)n && r > 8) continue;
+            if (r + 6 < (int)base.range_log2) break;  // far below the heuristic: only more path walks
+            rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);  // warm-up
+            if (rc != PIR_OK) break;
+            cudaEventRecord(a, s);
+            for (int i = 0; i < 3 && rc == PIR_OK; ++i) rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);
+            cudaEventRecord(b, s);
+            cudaError_t e = cudaEventSynchronize(b);
+            if (rc != PIR_OK) break;
+            if (e != cudaSuccess) {
+                rc = cuda_fail((int)e, "autotune sync");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms /= 3.f;
+            if (best_t < 0.f || ms < best_t) {
+                best_t = ms;
+                best = pl;
+            }
+        }
+        if (rc != PIR_OK) break;
+        if (g == 1) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != PIR_OK) return rc;
+    const uint32_t nqg = (uint32_t)((batch + best.group - 1) / best.group);
+    best.ctas = (uint32_t)std::min<uint64_t>((((t->rows - 1) >> best.range_log2) + 1) * nqg,
+                                             (uint64_t)std::max(1, device_sm_count()));
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        g_tuned[shape_key(t->rows, t->width, batch, v)] = best;
+    }
+    *best_plan = best;
+    if (best_ms) *best_ms = best_t;
+    return PIR_OK;
 }
 
 int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, uint32_t* dstatus,

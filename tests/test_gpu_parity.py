@@ -110,6 +110,25 @@ def test_every_launch_shape_matches_oracle(env):
     assert ran >= 80
 
 
+def test_autotuned_plan_is_used_and_exact(env):
+    torch, pir, orc = env
+    rows, width, batch = (1 << 15) + 9, 32, 12
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(44, rows, width)
+    alphas = wl.alphas(44, rows, batch)
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 44)
+    table = dev_table(torch, T)
+    dk = dev_keys(torch, ks0)
+    out = torch.empty((batch, width), dtype=torch.int32, device="cuda")
+    plan, ms = pir.pir_autotune(table, dk, batch, out)
+    assert ms > 0 and plan.group in (1, 2, 4, 8) and 1 <= plan.range_log2 <= n
+    chosen = pir.pir_plan_for(rows, width, batch)  # the cache answers for this shape now
+    assert (chosen.group, chosen.range_log2, chosen.vec) == (plan.group, plan.range_log2, plan.vec)
+    got = run_device(torch, pir, table, ks0, width)
+    for q in range(batch):
+        assert np.array_equal(got[q], orc.answer(ks0[q], T))
+
+
 def test_host_entry_point_host_and_device_outputs(env):
     torch, pir, orc = env
     rows, width, batch = 5000, 8, 6
