@@ -41,8 +41,15 @@
 namespace pir {
 namespace dev {
 
+// Tuning knobs (compile-time): consumer warps per CTA, leaf pairs per hand-off.
+#ifndef PIR_CONSUMER_WARPS
+#define PIR_CONSUMER_WARPS 4
+#endif
+#ifndef PIR_PAIRS_PER_PHASE
+#define PIR_PAIRS_PER_PHASE 2
+#endif
 constexpr int kProducers = 512;                             // threads that expand the tree
-constexpr int kConsumers = 128;                             // threads that multiply into the table
+constexpr int kConsumers = 32 * PIR_CONSUMER_WARPS;         // threads that multiply into the table
 constexpr int kFusedThreads = kProducers + kConsumers;
 constexpr int kMaxChunks = kConsumers;                      // W / VEC limit of the fused product
 constexpr int kPlaneBytes = 256 * 256;                     // 256 rows x [32 copies of Te_a | 32 of Te_b]
@@ -51,7 +58,7 @@ constexpr int kStackLevels = 8;                            // pending siblings p
 constexpr int kMaxDfsDepth = kStackLevels + 1;             // levels a thread expands on its own
 constexpr int kStackOff = kTablesBytes;
 constexpr int kStackBytes = kStackLevels * kProducers * 16;  // 64 KiB
-constexpr int kPairs = 2;                                  // leaf pairs per subtree between MAC phases
+constexpr int kPairs = PIR_PAIRS_PER_PHASE;                // leaf pairs per subtree between MAC phases
 constexpr int kYOff = kStackOff + kStackBytes;
 constexpr int kYWords = 2 * 2 * kPairs * kProducers;       // two buffers of G x 2kPairs x SQ words
 constexpr int kHdrOff = kYOff + 4 * kYWords;
