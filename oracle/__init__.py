@@ -62,6 +62,12 @@ def _load():
         lib.orc_key_bytes.restype = ctypes.c_size_t
         lib.orc_gen.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, u8p, u8p, u8p, u8p, u8p]
         lib.orc_gen.restype = ctypes.c_int
+        lib.orc_gen_prf.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, u8p, u8p, u8p,
+                                    u8p, u8p]
+        lib.orc_gen_prf.restype = ctypes.c_int
+        lib.orc_chacha20_block.argtypes = [u8p, ctypes.c_uint32, u8p, u8p]
+        lib.orc_chacha_quarter_round.argtypes = [u32p, u32p, u32p, u32p]
+        lib.orc_prf_id.argtypes = [ctypes.c_int, u8p, ctypes.c_uint8, u8p]
         lib.orc_eval.argtypes = [u8p, ctypes.c_uint64, u32p]
         lib.orc_eval.restype = ctypes.c_int
         lib.orc_full_eval.argtypes = [u8p, ctypes.c_uint64, u32p]
@@ -120,11 +126,30 @@ def aes128_encrypt(key: bytes, block: bytes) -> bytes:
     return out.tobytes()
 
 
-def prf(seed: bytes, x: int) -> bytes:
+def prf(seed: bytes, x: int, prf_id: int = 0) -> bytes:
+    """PRF_seed(x): prf_id 0 = AES-128, 1 = ChaCha20 (see dpf_oracle.c)."""
     s, sp = _u8(seed)
     out = np.zeros(16, np.uint8)
-    _load().orc_prf(sp, x, _u8(out)[1])
+    _load().orc_prf_id(prf_id, sp, x, _u8(out)[1])
     return out.tobytes()
+
+
+PRF_AES128, PRF_CHACHA20 = 0, 1
+
+
+def chacha20_block(key: bytes, counter: int, nonce: bytes) -> bytes:
+    """RFC 8439 Sec. 2.3 block function: 64 bytes."""
+    k, kp = _u8(key)
+    nn, np_ = _u8(nonce)
+    out = np.zeros(64, np.uint8)
+    _load().orc_chacha20_block(kp, counter, np_, _u8(out)[1])
+    return out.tobytes()
+
+
+def chacha_quarter_round(a: int, b: int, c: int, d: int):
+    v = [ctypes.c_uint32(x) for x in (a, b, c, d)]
+    _load().orc_chacha_quarter_round(*[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
 
 
 # ---------------------------------------------------------------- DPF
@@ -133,7 +158,7 @@ def key_bytes(n: int) -> int:
     return int(_load().orc_key_bytes(n))
 
 
-def gen(n: int, alpha: int, beta: int, seed0: bytes, seed1: bytes, rand_c0: bytes):
+def gen(n: int, alpha: int, beta: int, seed0: bytes, seed1: bytes, rand_c0: bytes, prf_id: int = 0):
     """Gen with explicit randomness: two 16-byte roots and n*2*16 codeword bytes."""
     if len(seed0) != 16 or len(seed1) != 16 or len(rand_c0) != 32 * n:
         raise ValueError("gen randomness has the wrong size")
@@ -143,7 +168,7 @@ def gen(n: int, alpha: int, beta: int, seed0: bytes, seed1: bytes, rand_c0: byte
     s0, s0p = _u8(seed0)
     s1, s1p = _u8(seed1)
     rc, rcp = _u8(rand_c0)
-    _check(_load().orc_gen(n, alpha, beta & 0xFFFFFFFF, s0p, s1p, rcp, _u8(k0)[1], _u8(k1)[1]), "gen")
+    _check(_load().orc_gen_prf(n, alpha, beta & 0xFFFFFFFF, prf_id, s0p, s1p, rcp, _u8(k0)[1], _u8(k1)[1]), "gen")
     return k0.tobytes(), k1.tobytes()
 
 

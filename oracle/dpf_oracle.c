@@ -13,6 +13,9 @@
  *     definition (multiplicative inverse, then the affine map), not typed in.
  *   - PRF_s(x) = AES-128 under key s of the block (x, 0, ..., 0) (Sec. 3.1,
  *     text under Eq. p3: "encrypts a message x with an encryption key s").
+ *     Alternative PRF (Sec. 3.2.6, Table 5): ChaCha20 (RFC 8439 Sec. 2.1-2.3),
+ *     block 0 under key s || 0^128 and an all-zero nonce, PRF_s(x) = its 16
+ *     bytes at offset 16x.  The key header names the PRF.
  *   - Eval: the recurrence of Eqs. p1-p3 (Sec. 3.1), "+" read as XOR in
  *     F_{2^128}, "P mod 2" read as the node's least-significant bit, path bits
  *     most-significant first (parent of node j is floor(j/2)).
@@ -29,7 +32,7 @@
  *
  * Key wire format (little-endian), shared as an interface with the library:
  *   [0,4)   magic "DPFK"      [4] version = 1     [5] n      [6] party sigma
- *   [7]     0                 [8,12) cw_out (u32) [12,16) 0
+ *   [7]     PRF (0 AES-128, 1 ChaCha20)  [8,12) cw_out (u32) [12,16) 0
  *   [16,32) root seed of this party
  *   then for d = 1..n: C_0[0][d], C_0[1][d], C_1[0][d], C_1[1][d] (16 B each)
  *   total 32 + 64 n bytes.
@@ -189,13 +192,84 @@ void orc_aes128_encrypt(const uint8_t key[16], const uint8_t in[16], uint8_t out
 }
 
 /* ------------------------------------------------------------------ */
+/* ChaCha20 (RFC 8439): Sec. 2.1 quarter round, Sec. 2.3 block function. */
+
+static uint32_t rotl32(uint32_t v, int c) { return (v << c) | (v >> (32 - c)); }
+
+void orc_chacha_quarter_round(uint32_t* a, uint32_t* b, uint32_t* c, uint32_t* d)
+{
+    *a += *b; *d ^= *a; *d = rotl32(*d, 16);
+    *c += *d; *b ^= *c; *b = rotl32(*b, 12);
+    *a += *b; *d ^= *a; *d = rotl32(*d, 8);
+    *c += *d; *b ^= *c; *b = rotl32(*b, 7);
+}
+
+static void quarter_round_on(uint32_t x[16], int a, int b, int c, int d)
+{
+    orc_chacha_quarter_round(&x[a], &x[b], &x[c], &x[d]);
+}
+
+void orc_chacha20_block(const uint8_t key[32], uint32_t counter, const uint8_t nonce[12], uint8_t out[64])
+{
+    /* Sec. 2.3: constants "expand 32-byte k", key, block counter, nonce; all little-endian words */
+    uint32_t state[16];
+    state[0] = 0x61707865;
+    state[1] = 0x3320646e;
+    state[2] = 0x79622d32;
+    state[3] = 0x6b206574;
+    for (int i = 0; i < 8; i++)
+        state[4 + i] = (uint32_t)key[4 * i] | ((uint32_t)key[4 * i + 1] << 8) | ((uint32_t)key[4 * i + 2] << 16) |
+                       ((uint32_t)key[4 * i + 3] << 24);
+    state[12] = counter;
+    for (int i = 0; i < 3; i++)
+        state[13 + i] = (uint32_t)nonce[4 * i] | ((uint32_t)nonce[4 * i + 1] << 8) |
+                        ((uint32_t)nonce[4 * i + 2] << 16) | ((uint32_t)nonce[4 * i + 3] << 24);
+    uint32_t x[16];
+    memcpy(x, state, sizeof(x));
+    for (int i = 0; i < 10; i++) { /* 20 rounds: column round then diagonal round */
+        quarter_round_on(x, 0, 4, 8, 12);
+        quarter_round_on(x, 1, 5, 9, 13);
+        quarter_round_on(x, 2, 6, 10, 14);
+        quarter_round_on(x, 3, 7, 11, 15);
+        quarter_round_on(x, 0, 5, 10, 15);
+        quarter_round_on(x, 1, 6, 11, 12);
+        quarter_round_on(x, 2, 7, 8, 13);
+        quarter_round_on(x, 3, 4, 9, 14);
+    }
+    for (int i = 0; i < 16; i++) {
+        uint32_t v = x[i] + state[i];
+        out[4 * i] = (uint8_t)v;
+        out[4 * i + 1] = (uint8_t)(v >> 8);
+        out[4 * i + 2] = (uint8_t)(v >> 16);
+        out[4 * i + 3] = (uint8_t)(v >> 24);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* The PRF of Eq. p3: PRF_s(x) encrypts message x under key s.          */
+/* prf 0: AES-128 of the block (x, 0, ..., 0) under key s.              */
+/* prf 1: ChaCha20 block 0 under key s || 0^128 with nonce 0; PRF_s(x)  */
+/*        is its 16 bytes at offset 16x (one block serves both x).      */
+
+enum { PRF_AES128 = 0, PRF_CHACHA20 = 1 };
 
 void orc_prf(const uint8_t s[16], uint8_t x, uint8_t out[16])
 {
     uint8_t msg[16] = {0};
     msg[0] = x;
     orc_aes128_encrypt(s, msg, out);
+}
+
+void orc_prf_id(int prf, const uint8_t s[16], uint8_t x, uint8_t out[16])
+{
+    if (prf == PRF_CHACHA20) {
+        uint8_t key[32] = {0}, nonce[12] = {0}, block[64];
+        memcpy(key, s, 16);
+        orc_chacha20_block(key, 0, nonce, block);
+        memcpy(out, block + 16 * x, 16);
+    } else {
+        orc_prf(s, x, out);
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -233,7 +307,7 @@ int orc_key_parse(const uint8_t* key, uint32_t* n, uint32_t* party, uint32_t* cw
 {
     if (key[0] != 'D' || key[1] != 'P' || key[2] != 'F' || key[3] != 'K' || key[4] != 1)
         return ORC_ERR_KEY;
-    if (key[5] < 1 || key[5] > 63 || key[6] > 1)
+    if (key[5] < 1 || key[5] > 63 || key[6] > 1 || key[7] > PRF_CHACHA20)
         return ORC_ERR_KEY;
     *n = key[5];
     *party = key[6];
@@ -246,9 +320,11 @@ int orc_key_parse(const uint8_t* key, uint32_t* n, uint32_t* party, uint32_t* cw
 /* All randomness is an input: seed0/seed1 (roots, lsb forced to 0/1)   */
 /* and rand_c0 = n x 2 x 16 bytes for the codewords C_0[b][d].          */
 
-int orc_gen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t seed0[16], const uint8_t seed1[16],
-            const uint8_t* rand_c0, uint8_t* key0, uint8_t* key1)
+int orc_gen_prf(uint32_t n, uint64_t alpha, uint32_t beta, int prf, const uint8_t seed0[16],
+                const uint8_t seed1[16], const uint8_t* rand_c0, uint8_t* key0, uint8_t* key1)
 {
+    if (prf != PRF_AES128 && prf != PRF_CHACHA20)
+        return ORC_ERR_ARG;
     if (n < 1 || n > 63 || (n < 64 && (alpha >> n) != 0))
         return ORC_ERR_ARG;
     size_t kb = orc_key_bytes(n);
@@ -267,7 +343,7 @@ int orc_gen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t seed0[16], 
         uint8_t c[2][2][16]; /* c[party][b] = PRF_{v_party}(b) */
         for (int p = 0; p < 2; p++)
             for (int b = 0; b < 2; b++)
-                orc_prf(v[p], (uint8_t)b, c[p][b]);
+                orc_prf_id(prf, v[p], (uint8_t)b, c[p][b]);
 
         /* seed correction: makes the off-path children equal */
         uint8_t s_cw[16];
@@ -316,11 +392,18 @@ int orc_gen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t seed0[16], 
         k[4] = 1;
         k[5] = (uint8_t)n;
         k[6] = (uint8_t)p;
+        k[7] = (uint8_t)prf;
         put_u32(k + 8, cw_out);
         memcpy(k + 16, p == 0 ? seed0 : seed1, 16);
         k[16] = p == 0 ? (uint8_t)(k[16] & 0xfe) : (uint8_t)(k[16] | 0x01);
     }
     return ORC_OK;
+}
+
+int orc_gen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t seed0[16], const uint8_t seed1[16],
+            const uint8_t* rand_c0, uint8_t* key0, uint8_t* key1)
+{
+    return orc_gen_prf(n, alpha, beta, PRF_AES128, seed0, seed1, rand_c0, key0, key1);
 }
 
 /* ------------------------------------------------------------------ */
@@ -345,7 +428,7 @@ int orc_eval(const uint8_t* key, uint64_t j, uint32_t* y)
     for (uint32_t d = 1; d <= n; d++) {
         int b = (int)((j >> (n - d)) & 1); /* "j mod 2" of the depth-d ancestor */
         uint8_t prf[16];
-        orc_prf(v, (uint8_t)b, prf);
+        orc_prf_id(key[7], v, (uint8_t)b, prf);
         const uint8_t* cw = codeword(key, d, lsb(v), b);
         for (int i = 0; i < 16; i++)
             v[i] = (uint8_t)(prf[i] ^ cw[i]);
@@ -381,7 +464,7 @@ int orc_full_eval(const uint8_t* key, uint64_t L, uint32_t* y)
             const uint8_t* parent = level + 16 * (jd >> 1); /* P(d-1, floor(j/2)) */
             int b = (int)(jd & 1);                         /* j mod 2 */
             uint8_t prf[16];
-            orc_prf(parent, (uint8_t)b, prf);
+            orc_prf_id(key[7], parent, (uint8_t)b, prf);
             const uint8_t* cw = codeword(key, d, lsb(parent), b);
             for (int i = 0; i < 16; i++)
                 next[16 * jd + i] = (uint8_t)(prf[i] ^ cw[i]);
@@ -447,7 +530,7 @@ int orc_node(const uint8_t* key, uint32_t d, uint64_t j, uint8_t out[16])
     for (uint32_t e = 1; e <= d; e++) {
         int b = (int)((j >> (d - e)) & 1);
         uint8_t prf[16];
-        orc_prf(v, (uint8_t)b, prf);
+        orc_prf_id(key[7], v, (uint8_t)b, prf);
         const uint8_t* cw = codeword(key, e, lsb(v), b);
         for (int i = 0; i < 16; i++)
             v[i] = (uint8_t)(prf[i] ^ cw[i]);

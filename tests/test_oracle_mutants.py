@@ -39,6 +39,10 @@ MUTANTS = {
     "cw_out_sign": ("uint32_t cw_out = lsb(v[1]) ? (uint32_t)(0u - diff) : diff;", "uint32_t cw_out = diff;"),
     # inner product against the wrong column
     "answer_wrong_column": ("out[w] += y[j] * row[w];", "out[w] += y[j] * row[0];"),
+    # ChaCha20 quarter round with a wrong rotation
+    "chacha_rotation": ("*b ^= *c; *b = rotl32(*b, 12);", "*b ^= *c; *b = rotl32(*b, 13);"),
+    # ChaCha20 PRF taking the wrong slice of the block
+    "chacha_slice": ("memcpy(out, block + 16 * x, 16);", "memcpy(out, block + 32 * x, 16);"),
     # ShiftRows in the wrong direction
     "shiftrows_direction": ("tmp[r][c] = state[r][(c + r) % 4];", "tmp[r][c] = state[r][(c + 4 - r) % 4];"),
 }
@@ -54,7 +58,7 @@ def test_pins_catch_mutant(tmp_path, name):
         shutil.copytree(os.path.join(ROOT, sub), tmp_path / sub,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     (tmp_path / "tests").mkdir()
-    for f in ("conftest.py", "test_oracle_aes.py", "test_oracle_dpf.py"):
+    for f in ("conftest.py", "test_oracle_aes.py", "test_oracle_dpf.py", "test_oracle_chacha.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
     (tmp_path / "oracle" / "dpf_oracle.c").write_text(src.replace(old, new))
