@@ -55,6 +55,7 @@ WORKLOADS = {
 # Paper Table 4 (Sec. 5): 1M entries x 2048 bit, AES-128, one V100: 1,358 QPS (other hardware; context).
 PAPER_QPS = {"batched_1m": 1358.0}
 LOOKUPS_PER_NODE = 360  # table-lookup AES-128: 40 for the key expansion + 2 x 160 for the two blocks
+CHACHA_ALU_OPS_PER_NODE = 640  # ChaCha20 block: 20 rounds x 4 quarter rounds x (4 XOR + 4 rotate)
 
 
 # ----------------------------------------------------------------------------- distributed plumbing
@@ -178,7 +179,12 @@ def gpu_id_for(device) -> str | None:
 
 # ----------------------------------------------------------------------------- CPU oracle timing
 
-def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float = 20.0, max_wall_s: float = 60.0):
+PRFS = {"aes128": 0, "chacha20": 1}
+PRF_NAMES = {0: "AES-128", 1: "ChaCha20"}
+
+
+def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float = 20.0, max_wall_s: float = 60.0,
+               prf: int = 0):
     """Times the oracle (as it stands) on host threads: each thread evaluates whole
     queries (FullEval + inner product).  Returns (qps, threads, queries, wall)."""
     from concurrent.futures import ThreadPoolExecutor
@@ -193,7 +199,7 @@ def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float =
     queries = max(1, min(queries, int(max_wall_s / per_query_s) * threads))
     rnd = wl.key_randomness(seed + 1, n, queries)
     alphas = wl.alphas(seed + 1, rows, queries)
-    keys = [oracle.gen(n, int(a), 1, r0, r1, c0)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    keys = [oracle.gen(n, int(a), 1, r0, r1, c0, prf)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
         list(ex.map(lambda k: oracle.answer(k, table_np), keys))
@@ -240,7 +246,8 @@ class SingleTableWorkload:
         self.seed = seed
         self.table = wl.table_u32_torch(seed, self.rows, self.width, device)
         self.alphas = wl.alphas(seed, self.rows, self.batch)
-        self.pairs = [pir.pir_keygen(self.n, int(a), 1, hashlib.sha256(b"bench%d-%d" % (seed, q)).digest())
+        self.prf = PRFS[args.prf]
+        self.pairs = [pir.pir_keygen_prf(self.n, int(a), 1, self.prf, hashlib.sha256(b"bench%d-%d" % (seed, q)).digest())
                       for q, a in enumerate(self.alphas)]
         self.keys0 = b"".join(p[0] for p in self.pairs)
         self.keys1 = b"".join(p[1] for p in self.pairs)
@@ -275,7 +282,7 @@ class SingleTableWorkload:
 
     def config(self):
         return {"workload": self.desc, "rows": self.rows, "width_words": self.width, "batch": self.batch,
-                "n": self.n, "prf": "AES-128",
+                "n": self.n, "prf": PRF_NAMES[self.prf],
                 "l2": f"inputs larger than L2: table {self.rows * self.width * 4 >> 20} MiB per step, no flush"
                 if self.rows * self.width * 4 > 129e6 else "table fits in L2; no flush (resident-table serving)",
                 "plan": self.plan.as_dict()}
@@ -334,7 +341,8 @@ class SingleTableWorkload:
         return out
 
     def cpu_baseline(self):
-        qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, self.table.cpu().numpy().view(np.uint32))
+        qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, self.table.cpu().numpy().view(np.uint32),
+                                          prf=self.prf)
         return {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
                 "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
                           f"{cores} host threads, {wall:.1f} s wall"}
@@ -639,8 +647,18 @@ def run_ours(args):
     clocks = sampler.summary()
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     kernel_ms = statistics.mean(per_step)
-    achieved = LOOKUPS_PER_NODE * W.nodes_per_step / (kernel_ms / 1e3) / 1e9
-    peak = sms * 32 * max_mhz * 1e6 / 1e9
+    if getattr(W, "prf", 0) == 1:
+        # ChaCha20: the 640 XORs and rotations of 20 rounds per node run on the ALU pipe (64 lanes/clk/SM)
+        per_node, unit = CHACHA_ALU_OPS_PER_NODE, "Gop/s"
+        peak = sms * 64 * max_mhz * 1e6 / 1e9
+        work = f"{CHACHA_ALU_OPS_PER_NODE} ChaCha20 XOR/rotate ops x {W.nodes_per_step} tree nodes per launch"
+        basis = f"{sms} SMs x 64 ALU-pipe lanes/clk x {max_mhz:.0f} MHz (derived)"
+    else:
+        per_node, unit = LOOKUPS_PER_NODE, "Glookup/s"
+        peak = sms * 32 * max_mhz * 1e6 / 1e9
+        work = f"{LOOKUPS_PER_NODE} AES table lookups x {W.nodes_per_step} tree nodes per launch"
+        basis = f"{sms} SMs x 32 shared-memory lookups/clk x {max_mhz:.0f} MHz (derived)"
+    achieved = per_node * W.nodes_per_step / (kernel_ms / 1e3) / 1e9
     cfg = W.config()
     cfg["parallelism"] = f"{world} replica(s), independent queries"
     out = {
@@ -660,11 +678,10 @@ def run_ours(args):
         "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
                        "p99": round(float(np.percentile(per_step, 99)), 4)},
         "gpu_launches": steps,
-        "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Glookup/s",
-                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(args.workload),
-                     "kernel": W.kernel, "kernel_ms": round(kernel_ms, 4),
-                     "work": f"{LOOKUPS_PER_NODE} AES table lookups x {W.nodes_per_step} tree nodes per launch",
-                     "peak_basis": f"{sms} SMs x 32 shared-memory lookups/clk x {max_mhz:.0f} MHz (derived)"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": unit,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": profiled_traffic(args.workload) if getattr(W, "prf", 0) == 0 else None,
+                     "kernel": W.kernel, "kernel_ms": round(kernel_ms, 4), "work": work, "peak_basis": basis},
         "e2e": {"value": round(W.queries_per_step * world * e2e_steps / (e2e_total / 1e3), 2), "unit": "queries/s",
                 "h2d_bytes_per_step": W.h2d_bytes, "d2h_bytes_per_step": W.d2h_bytes,
                 "p50_ms": round(float(np.percentile(e2e_ms, 50)), 4), "bit_exact_vs_device": e2e_ok},
@@ -759,6 +776,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched_1m")
+    ap.add_argument("--prf", choices=sorted(PRFS), default="aes128",
+                    help="PRF of the keys (single-table workloads): AES-128 or ChaCha20 (Sec. 3.2.6, Table 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rates", default="1000,2000,4000,6000,10000,20000,50000,100000,200000",
                     help="serving workload: offered Poisson rates (queries/s)")

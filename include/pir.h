@@ -29,7 +29,7 @@
  *    of the 2^n-leaf tree are evaluated but never multiplied.
  *
  * Key wire format (32 + 64 n bytes, little-endian, 16-byte aligned fields):
- *   [0,4) "DPFK"  [4] version 1  [5] n  [6] party sigma (0/1)  [7] 0
+ *   [0,4) "DPFK"  [4] version 1  [5] n  [6] party sigma (0/1)  [7] PRF id
  *   [8,12) cw_out (u32)  [12,16) 0  [16,32) root seed P(0,0) of this party
  *   [32 + 64(d-1) + 32t + 16b, +16) = codeword C_t[b][d], d = 1..n, t,b in {0,1}
  * The 64 n codeword bytes are the paper's key size (Table 4: 896 B at 16K
@@ -60,6 +60,14 @@ extern "C" {
 
 #define PIR_KEY_HEADER_BYTES 32
 #define PIR_MAX_DOMAIN_BITS 40
+
+/* PRF of a key's tree (header byte 7).  AES-128: PRF_s(x) = AES-128_s of the
+ * block (x, 0, ..., 0) (Sec. 3.1, Sec. 3.2.6).  ChaCha20 (Sec. 3.2.6,
+ * Table 5): PRF_s(x) = bytes [16x, 16x+16) of ChaCha20 block 0 (RFC 8439)
+ * under key s || 0^128 with an all-zero nonce.  Every server entry point
+ * takes either, per key. */
+#define PIR_PRF_AES128 0u
+#define PIR_PRF_CHACHA20 1u
 
 /* A table resident in device memory: row j of the table (j counted from the
  * first row `data` points at) starts at data + j * stride.  data must be
@@ -98,6 +106,12 @@ uint32_t pir_domain_bits(uint64_t rows);
  * from the operating system's entropy source.  Errors: PIR_ERR_ARG (null
  * keys, n == 0 or n > 40), PIR_ERR_DOMAIN (alpha >= 2^n). */
 int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, uint8_t* key0, uint8_t* key1);
+
+/* pir_keygen with the tree's PRF chosen: PIR_PRF_AES128 (what pir_keygen
+ * uses) or PIR_PRF_CHACHA20.  Errors as pir_keygen; PIR_ERR_ARG for an
+ * unknown prf. */
+int pir_keygen_prf(uint32_t n, uint64_t alpha, uint32_t beta, uint32_t prf, const uint8_t* seed, uint8_t* key0,
+                   uint8_t* key1);
 
 /* Validates a key's header (magic, version, n, party, length == 32 + 64 n).
  * On success stores n and the party (0 or 1).  Errors: PIR_ERR_ARG,

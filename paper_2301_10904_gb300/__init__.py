@@ -68,6 +68,8 @@ def _load():
         "pir_key_bytes": (ctypes.c_size_t, [ctypes.c_uint32]),
         "pir_domain_bits": (ctypes.c_uint32, [ctypes.c_uint64]),
         "pir_keygen": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, u8p, u8p, u8p]),
+        "pir_keygen_prf": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p,
+                                          u8p, u8p]),
         "pir_key_check": (ctypes.c_int, [u8p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32),
                                          ctypes.POINTER(ctypes.c_uint32)]),
         "pir_reconstruct": (ctypes.c_int, [u32p, u32p, ctypes.c_size_t, u32p]),
@@ -154,15 +156,22 @@ def pir_domain_bits(rows: int) -> int:
     return int(_lib.pir_domain_bits(rows))
 
 
+PIR_PRF_AES128, PIR_PRF_CHACHA20 = 0, 1
+
+
 def pir_keygen(n: int, alpha: int, beta: int = 1, seed: bytes | None = None):
+    return pir_keygen_prf(n, alpha, beta, PIR_PRF_AES128, seed)
+
+
+def pir_keygen_prf(n: int, alpha: int, beta: int = 1, prf: int = PIR_PRF_AES128, seed: bytes | None = None):
     kb = pir_key_bytes(n)
     k0 = ctypes.create_string_buffer(kb)
     k1 = ctypes.create_string_buffer(kb)
     if seed is not None and len(seed) != 32:
         raise ValueError("seed must be 32 bytes")
     sp = _buf(seed) if seed is not None else None
-    _check(_lib.pir_keygen(n, alpha, beta & 0xFFFFFFFF, sp, ctypes.cast(k0, ctypes.c_void_p),
-                           ctypes.cast(k1, ctypes.c_void_p)), "pir_keygen")
+    _check(_lib.pir_keygen_prf(n, alpha, beta & 0xFFFFFFFF, prf, sp, ctypes.cast(k0, ctypes.c_void_p),
+                               ctypes.cast(k1, ctypes.c_void_p)), "pir_keygen_prf")
     return k0.raw, k1.raw
 
 

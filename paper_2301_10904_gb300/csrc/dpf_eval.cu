@@ -6,7 +6,7 @@
 //   P(0,0) = root;  P(d,j) = AES_{P(d-1,j>>1)}((j&1) || 0^120) ^ C_t[j&1][d],
 //   t = lsb(P(d-1,j>>1));  y(j) = (-1)^sigma (word1(P(n,j)) + lsb(P(n,j)) * cw_out).
 //
-// Structure.  One CTA per SM (512 producer + 128 consumer threads), persistent
+// Structure.  One CTA per SM (512 producer + 256 consumer threads), persistent
 // over work items; an item is G queries x 2^r consecutive rows.
 //  1. lookup tables, built once per CTA: the S-box derived from GF(2^8), the
 //     four AES column tables Te0..Te3 (Te_r = rotl(Te0, 8r)), each with 32
@@ -24,7 +24,7 @@
 //     bytes that the share needs are computed in the last round.
 //  5. warp-specialised fusion (Sec. 3.2.4): 16 producer warps run steps 2-4
 //     and drop every kPairs leaf pairs' shares into one of two shared-memory
-//     buffers; 4 consumer warps multiply each buffer, for all G queries at
+//     buffers; 8 consumer warps multiply each buffer, for all G queries at
 //     once, into register accumulators against the table rows it indexes
 //     (each row read once per CTA), while the producers fill the other
 //     buffer.  Named barriers pass the buffers back and forth.
@@ -43,10 +43,10 @@ namespace dev {
 
 // Tuning knobs (compile-time): consumer warps per CTA, leaf pairs per hand-off.
 #ifndef PIR_CONSUMER_WARPS
-#define PIR_CONSUMER_WARPS 4
+#define PIR_CONSUMER_WARPS 8
 #endif
 #ifndef PIR_PAIRS_PER_PHASE
-#define PIR_PAIRS_PER_PHASE 2
+#define PIR_PAIRS_PER_PHASE 4
 #endif
 constexpr int kProducers = 512;                             // threads that expand the tree
 constexpr int kConsumers = 32 * PIR_CONSUMER_WARPS;         // threads that multiply into the table
@@ -61,11 +61,17 @@ constexpr int kStackBytes = kStackLevels * kProducers * 16;  // 64 KiB
 constexpr int kPairs = PIR_PAIRS_PER_PHASE;                // leaf pairs per subtree between MAC phases
 constexpr int kYOff = kStackOff + kStackBytes;
 constexpr int kYWords = 2 * 2 * kPairs * kProducers;       // two buffers of G x 2kPairs x SQ words
-constexpr int kHdrOff = kYOff + 4 * kYWords;
+// The same region first holds the split phase's two node buffers (kProducers
+// uint4 each) and at the end the per-item reduction (G x W words): size it
+// for the largest of the three uses.
+constexpr int kSplitWords = 2 * kProducers * 4;
+constexpr int kYRegionWords = kYWords > kSplitWords ? kYWords : kSplitWords;
+constexpr int kHdrOff = kYOff + 4 * kYRegionWords;
 constexpr int kMaxGroup = 8;
 constexpr int kHdrBytes = 32 * kMaxGroup;                  // per query: key ptr, out ptr, ok, party, cw_out
 constexpr int kItemOff = kHdrOff + kHdrBytes;              // work-item index broadcast (multi-table kernel)
 constexpr int kSmemBytes = kItemOff + 16;
+static_assert(kSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
 
 // The kernel's only shared memory; naming the array (not a pointer to it) in
 // every access lets the compiler address it as shared with an immediate base.
@@ -95,7 +101,7 @@ struct FusedParams {
 struct QueryHdr {  // one per query slot of the current item, in shared memory
     const uint8_t* key;
     uint32_t* out;
-    uint32_t ok, party, cw_out, pad;
+    uint32_t ok, party, cw_out, prf;
 };
 
 __device__ __forceinline__ QueryHdr* hdr_slot(int g) { return reinterpret_cast<QueryHdr*>(sm + kHdrOff) + g; }
@@ -224,15 +230,40 @@ __device__ __forceinline__ void prf2(const uint32_t lane4, const uint32_t lane4h
     }
 }
 
+// Both children under the ChaCha20 PRF: block 0 of ChaCha20 (RFC 8439) with
+// key v || 0^128, counter 0, nonce 0; words 0..3 are child 0, 4..7 child 1.
+#define CHACHA_QR(a, b, c, d)                                    \
+    a += b; d ^= a; d = __byte_perm(d, 0u, 0x1032u);             \
+    c += d; b ^= c; b = __funnelshift_l(b, b, 12);               \
+    a += b; d ^= a; d = __byte_perm(d, 0u, 0x2103u);             \
+    c += d; b ^= c; b = __funnelshift_l(b, b, 7);
+__device__ __forceinline__ void prf2_chacha(const uint4 v, uint4& c0, uint4& c1) {
+    constexpr uint32_t K0 = 0x61707865u, K1 = 0x3320646eu, K2 = 0x79622d32u, K3 = 0x6b206574u;
+    uint32_t x0 = K0, x1 = K1, x2 = K2, x3 = K3, x4 = v.x, x5 = v.y, x6 = v.z, x7 = v.w;
+    uint32_t x8 = 0, x9 = 0, x10 = 0, x11 = 0, x12 = 0, x13 = 0, x14 = 0, x15 = 0;
+#pragma unroll 2
+    for (int i = 0; i < 10; ++i) {
+        CHACHA_QR(x0, x4, x8, x12) CHACHA_QR(x1, x5, x9, x13) CHACHA_QR(x2, x6, x10, x14) CHACHA_QR(x3, x7, x11, x15)
+        CHACHA_QR(x0, x5, x10, x15) CHACHA_QR(x1, x6, x11, x12) CHACHA_QR(x2, x7, x8, x13) CHACHA_QR(x3, x4, x9, x14)
+    }
+    c0 = make_uint4(x0 + K0, x1 + K1, x2 + K2, x3 + K3);
+    c1 = make_uint4(x4 + v.x, x5 + v.y, x6 + v.z, x7 + v.w);
+}
+#undef CHACHA_QR
+
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
 
-// Children of v at depth d (1-based) of `key`: AES plus C_{lsb(v)}[b][d].
+// Children of v at depth d (1-based) of `key`: PRF plus C_{lsb(v)}[b][d].
+// `chacha` selects the key's PRF (uniform per query, so per warp in the DFS).
 __device__ __forceinline__ void expand(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
-                                       bool leaf, uint4& c0, uint4& c1) {
+                                       bool leaf, bool chacha, uint4& c0, uint4& c1) {
     // the codewords' address is known before the PRF: issue the loads first
     const uint4* cw = reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) + 32u * (v.x & 1u));
     const uint4 w0 = __ldg(cw), w1 = __ldg(cw + 1);
-    prf2(lane4, lane4h, v, leaf, c0, c1);
+    if (chacha)
+        prf2_chacha(v, c0, c1);
+    else
+        prf2(lane4, lane4h, v, leaf, c0, c1);
     c0 = xor4(c0, w0);
     c1 = xor4(c1, w1);
 }
@@ -340,6 +371,8 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
     constexpr int NT = MAT ? kProducers : kFusedThreads;
     static_assert(G * 2 * kPairs * SQ * 2 <= kYWords, "share buffers exceed their region");
+    static_assert(2 * kProducers * (int)sizeof(uint4) <= 4 * kYRegionWords, "split buffers exceed their region");
+    static_assert(kMaxGroup * 512 <= kYRegionWords, "reduction of the widest supported rows exceeds its region");
     static_assert(G <= kMaxGroup, "too many query slots");
 
     const int tid = threadIdx.x;
@@ -355,21 +388,22 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     uint4* bufB = bufA + kProducers;
     if (tid < G) {
         QueryHdr* h = hdr_slot(tid);
-        uint32_t ok = 0, party = 0, cwo = 0;
+        uint32_t ok = 0, party = 0, cwo = 0, prf = 0;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (h->key) {
             const uint8_t* key = h->key;
             const uint4 hw = __ldg(reinterpret_cast<const uint4*>(key));
             ok = hw.x == kKeyMagic && (hw.y & 0xffu) == kKeyVersion && ((hw.y >> 8) & 0xffu) == p.n &&
-                 ((hw.y >> 16) & 0xffu) <= 1u && (hw.y >> 24) == 0u;
+                 ((hw.y >> 16) & 0xffu) <= 1u && (hw.y >> 24) <= PIR_PRF_CHACHA20;
             if (ok) {
                 party = (hw.y >> 16) & 1u;
+                prf = hw.y >> 24;
                 cwo = hw.z;
                 v = __ldg(reinterpret_cast<const uint4*>(key + 16));
                 for (int d = 1; d <= n - r; ++d) {
                     const uint32_t b = (uint32_t)(r0 >> (n - d)) & 1u;
                     uint4 c0, c1;
-                    expand(lane4, lane4h, key, (uint32_t)d, v, false, c0, c1);
+                    expand(lane4, lane4h, key, (uint32_t)d, v, false, prf != 0, c0, c1);
                     v = b ? c1 : c0;
                 }
             } else if (p.status) {
@@ -379,6 +413,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         h->ok = ok;
         h->party = party;
         h->cw_out = cwo;
+        h->prf = prf;
         bufA[tid] = v;
     }
     __syncthreads();
@@ -392,7 +427,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
             const uint4 v = src[tid];
             uint4 c0 = v, c1 = v;
             const QueryHdr* h = hdr_slot(g);
-            if (h->ok) expand(lane4, lane4h, h->key, (uint32_t)(n - r + i + 1), v, false, c0, c1);
+            if (h->ok) expand(lane4, lane4h, h->key, (uint32_t)(n - r + i + 1), v, false, h->prf != 0, c0, c1);
             dst[(g << (i + 1)) + 2 * idx] = c0;
             dst[(g << (i + 1)) + 2 * idx + 1] = c1;
         }
@@ -418,6 +453,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     if (producer) {
         // ---- depth-first expansion; hand over shares every kc leaf pairs ----
         const uint32_t party = hq->party, cwo = hq->cw_out;
+        const bool chacha = hq->prf != 0;
         const uint8_t* key = hq->key;
         const int d0 = n - r + sd;  // depth of this thread's subtree root
         int lvl = 0;
@@ -425,7 +461,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         for (;;) {
             const bool leaf = lvl + 1 == m;
             uint4 c0 = node, c1 = node;
-            if (act) expand(lane4, lane4h, key, (uint32_t)(d0 + lvl + 1), node, leaf, c0, c1);
+            if (act) expand(lane4, lane4h, key, (uint32_t)(d0 + lvl + 1), node, leaf, chacha, c0, c1);
             if (leaf) {
                 uint32_t y0 = 0, y1 = 0;
                 if (act) {
@@ -609,7 +645,7 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     if (plan.vec != 1 && plan.vec != 4) return PIR_ERR_UNSUPPORTED;
     if (plan.vec == 4 && (!vec_ok || width % 4 != 0)) return PIR_ERR_UNSUPPORTED;
     if (width == 0 || width / plan.vec > (uint32_t)dev::kMaxChunks) return PIR_ERR_UNSUPPORTED;
-    if ((uint64_t)plan.group * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
+    if ((uint64_t)plan.group * width > (uint64_t)dev::kYRegionWords) return PIR_ERR_UNSUPPORTED;
     const int r = (int)plan.range_log2;
     if (r < 1 || r > (int)n) return PIR_ERR_UNSUPPORTED;
     const int sd = std::min(log_sq(plan.group), r - 1);
@@ -624,8 +660,8 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     pl.vec = (vec_ok && width % 4 == 0) ? 4 : 1;
     if (width / pl.vec > (uint32_t)dev::kMaxChunks) return PIR_ERR_UNSUPPORTED;
     uint32_t g = 8;
-    while (g > 1 && (g > batch || (uint64_t)g * width > (uint64_t)dev::kYWords)) g >>= 1;
-    if ((uint64_t)g * width > (uint64_t)dev::kYWords) return PIR_ERR_UNSUPPORTED;
+    while (g > 1 && (g > batch || (uint64_t)g * width > (uint64_t)dev::kYRegionWords)) g >>= 1;
+    if ((uint64_t)g * width > (uint64_t)dev::kYRegionWords) return PIR_ERR_UNSUPPORTED;
     pl.group = g;
     const uint32_t nqg = (batch + g - 1) / g;
     const int lsq = log_sq(g);

@@ -71,8 +71,33 @@ bool os_entropy(uint8_t* out, size_t len) {
     return true;
 }
 
-// Both children of a node: out[b] = AES_node(b || 0^120).
-void prf_pair(const uint8_t node[16], uint8_t out[2][16]) {
+// ChaCha20 block 0 (RFC 8439) under key node || 0^128, nonce 0: the first
+// 32 bytes are the two children.
+void chacha_children(const uint8_t node[16], uint8_t out[2][16]) {
+    uint32_t s[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u};
+    for (int i = 0; i < 4; ++i) s[4 + i] = get_u32(node + 4 * i);
+    uint32_t x[16];
+    std::memcpy(x, s, sizeof(x));
+    auto rotl = [](uint32_t v, int c) { return (v << c) | (v >> (32 - c)); };
+    auto qr = [&](int a, int b, int c, int d) {
+        x[a] += x[b]; x[d] = rotl(x[d] ^ x[a], 16);
+        x[c] += x[d]; x[b] = rotl(x[b] ^ x[c], 12);
+        x[a] += x[b]; x[d] = rotl(x[d] ^ x[a], 8);
+        x[c] += x[d]; x[b] = rotl(x[b] ^ x[c], 7);
+    };
+    for (int r = 0; r < 10; ++r) {
+        qr(0, 4, 8, 12); qr(1, 5, 9, 13); qr(2, 6, 10, 14); qr(3, 7, 11, 15);
+        qr(0, 5, 10, 15); qr(1, 6, 11, 12); qr(2, 7, 8, 13); qr(3, 4, 9, 14);
+    }
+    for (int i = 0; i < 8; ++i) put_u32(out[i >> 2] + 4 * (i & 3), x[i] + s[i]);
+}
+
+// Both children of a node: out[b] = PRF_node(b) for the key's PRF.
+void prf_pair(const uint8_t node[16], uint32_t prf, uint8_t out[2][16]) {
+    if (prf == PIR_PRF_CHACHA20) {
+        chacha_children(node, out);
+        return;
+    }
     Aes128 a;
     a.set_key(node);
     uint8_t msg[16] = {0};
@@ -96,8 +121,14 @@ uint32_t pir_domain_bits(uint64_t rows) {
 }
 
 int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, uint8_t* key0, uint8_t* key1) {
+    return pir_keygen_prf(n, alpha, beta, PIR_PRF_AES128, seed, key0, key1);
+}
+
+int pir_keygen_prf(uint32_t n, uint64_t alpha, uint32_t beta, uint32_t prf, const uint8_t* seed, uint8_t* key0,
+                   uint8_t* key1) {
     using namespace pir;
     if (!key0 || !key1 || n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_ARG;
+    if (prf != PIR_PRF_AES128 && prf != PIR_PRF_CHACHA20) return PIR_ERR_ARG;
     if ((alpha >> n) != 0) return PIR_ERR_DOMAIN;
 
     // randomness: two roots and the shared codeword set C_0
@@ -125,8 +156,8 @@ int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, u
         const uint32_t on = (uint32_t)(alpha >> (n - d)) & 1u;  // child bit on the path
         const uint32_t off = on ^ 1u;
         uint8_t ch[2][2][16];  // ch[party][b]
-        prf_pair(node[0], ch[0]);
-        prf_pair(node[1], ch[1]);
+        prf_pair(node[0], prf, ch[0]);
+        prf_pair(node[1], prf, ch[1]);
         uint8_t delta[2][16];
         for (int i = 0; i < 16; ++i) delta[0][i] = delta[1][i] = ch[0][off][i] ^ ch[1][off][i];
         delta[0][0] &= 0xfe;
@@ -163,7 +194,7 @@ int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, u
         k[4] = (uint8_t)kKeyVersion;
         k[5] = (uint8_t)n;
         k[6] = (uint8_t)p;
-        k[7] = 0;
+        k[7] = (uint8_t)prf;
         put_u32(k + 8, corr);
         put_u32(k + 12, 0);
     }
@@ -175,7 +206,7 @@ int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, u
 int pir_key_check(const uint8_t* key, size_t len, uint32_t* n, uint32_t* party) {
     using namespace pir;
     if (!key || len < PIR_KEY_HEADER_BYTES) return PIR_ERR_ARG;
-    if (get_u32(key) != kKeyMagic || key[4] != kKeyVersion || key[7] != 0) return PIR_ERR_KEY;
+    if (get_u32(key) != kKeyMagic || key[4] != kKeyVersion || key[7] > PIR_PRF_CHACHA20) return PIR_ERR_KEY;
     const uint32_t kn = key[5], kp = key[6];
     if (kn == 0 || kn > PIR_MAX_DOMAIN_BITS || kp > 1) return PIR_ERR_KEY;
     if (len != key_bytes(kn)) return PIR_ERR_KEY;

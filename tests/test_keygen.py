@@ -91,3 +91,20 @@ def test_keygen_argument_errors(pir):
 def test_reconstruct_wraps_mod_2_32(pir):
     s = pir.pir_reconstruct(np.array([M32, 5], np.uint32), np.array([2, M32], np.uint32))
     assert s.tolist() == [1, 4]
+
+
+def test_library_chacha_keys_satisfy_identity_under_oracle(pir, orc):
+    for n in (1, 4, 9):
+        L = 1 << n
+        for alpha in (0, L - 1, L // 3):
+            k0, k1 = pir.pir_keygen_prf(n, alpha, 5, pir.PIR_PRF_CHACHA20, _seed(alpha + 3 * n))
+            assert k0[7] == 1 and k1[7] == 1 and pir.pir_key_check(k0) == (n, 0)
+            s = (orc.full_eval(k0, L).astype(np.uint64) + orc.full_eval(k1, L)) & M32
+            want = np.zeros(L, np.uint64)
+            want[alpha] = 5
+            assert np.array_equal(s, want)
+
+
+def test_keygen_rejects_unknown_prf(pir):
+    with pytest.raises(pir.PirError):
+        pir.pir_keygen_prf(4, 1, 1, 7, None)
