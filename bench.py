@@ -54,6 +54,18 @@ WORKLOADS = {
 }
 # Paper Table 4 (Sec. 5): 1M entries x 2048 bit, AES-128, one V100: 1,358 QPS (other hardware; context).
 PAPER_QPS = {"batched_1m": 1358.0}
+L2_BYTES = 129 * 1000 * 1000
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json),
+    else the recipe's fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "of measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback"
+
+
 LOOKUPS_PER_NODE = 360  # table-lookup AES-128: 40 for the key expansion + 2 x 160 for the two blocks
 CHACHA_ALU_OPS_PER_NODE = 640  # ChaCha20 block: 20 rounds x 4 quarter rounds x (4 XOR + 4 rotate)
 
@@ -338,7 +350,42 @@ class SingleTableWorkload:
                                    "share_matrix_bytes": s_bytes,
                                    "bit_exact_vs_fused": {"imad": ok_imad, "mma_u8": ok_mma}}
             del S
+        if self.args.scan and self.width % 4 == 0 and self.rows * self.width * 4 > 2 * L2_BYTES:
+            out["scan"] = self.scan_roofline()
         return out
+
+    def scan_roofline(self):
+        """The streaming scan engine (PIR_CONTRACT_SCAN) on the materialised shares
+        of 1 and 8 queries: HBM bytes (table + shares + out) per launch / launch time."""
+        torch, pir, stream = self.torch, self.pir, self.stream
+        peak, basis = measured_hbm_gbs()
+        res = {}
+        for q in (1, 8):
+            if q > self.batch:
+                continue
+            S = torch.empty((q, self.rows), dtype=torch.int32, device=self.device)
+            pir.pir_expand_materialise(self.rows, self.dkeys[:q * self.kb], q, S, stream=stream)
+            a = torch.empty((q, self.width), dtype=torch.int32, device=self.device)
+            b = torch.empty_like(a)
+            pir.pir_contract_u32(S, q, self.table, b, engine=pir.PIR_CONTRACT_IMAD, stream=stream)
+            for _ in range(3):
+                pir.pir_contract_u32(S, q, self.table, a, engine=pir.PIR_CONTRACT_SCAN, stream=stream)
+            reps = 20
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+            for i in range(reps):
+                ev[2 * i].record(stream)
+                pir.pir_contract_u32(S, q, self.table, a, engine=pir.PIR_CONTRACT_SCAN, stream=stream)
+                ev[2 * i + 1].record(stream)
+            ev[-1].synchronize()
+            ms = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps))
+            nbytes = self.rows * self.width * 4 + q * self.rows * 4 + q * self.width * 4
+            gbs = nbytes / (ms / 1e3) / 1e9
+            res[f"q{q}"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(gbs / peak, 4), "ms": round(ms, 4), "bytes_per_launch": nbytes,
+                            "kernel": "contract_scan_kernel", "bit_exact_vs_imad": bool(torch.equal(a, b)),
+                            "faults": pir.pir_device_status(), "peak_basis": basis}
+            del S
+        return res
 
     def cpu_baseline(self):
         qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, self.table.cpu().numpy().view(np.uint32),
@@ -785,6 +832,8 @@ def main(argv=None):
     ap.add_argument("--max-requests", type=int, default=8000, help="serving workload: requests per rate, at most")
     ap.add_argument("--no-materialised", dest="materialised", action="store_false",
                     help="skip the materialised (share matrix in HBM) comparison leg")
+    ap.add_argument("--no-scan", dest="scan", action="store_false",
+                    help="skip the streaming-scan (HBM roofline) leg on tables larger than L2")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

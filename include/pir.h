@@ -10,7 +10,7 @@
  *   client: T[alpha] * beta = share_0 + share_1 (mod 2^32)   (Sec. 3.1)
  *
  * All table, share and output arithmetic is integer mod 2^32; all tree
- * arithmetic is 128-bit XOR with AES-128 as the PRF (Sec. 3.2.6).
+ * arithmetic is 128-bit XOR with AES-128 or ChaCha20 as the PRF (Sec. 3.2.6).
  *
  * Conventions for every entry point:
  *  - Plain pointers and sizes only.  "device" pointers are CUDA device
@@ -57,6 +57,9 @@ extern "C" {
 #define PIR_ERR_UNSUPPORTED (-8) /* shape outside the kernels' limits */
 
 #define PIR_STATUS_BAD_KEY 1u    /* device status bit: some key failed validation */
+#define PIR_STATUS_SMEM_LAYOUT 2u /* device status bit: a kernel found its shared memory at an
+                                     unexpected window offset and did nothing (the host checks the
+                                     device's reserved shared memory first, so this is a guard) */
 
 #define PIR_KEY_HEADER_BYTES 32
 #define PIR_MAX_DOMAIN_BITS 40
@@ -129,8 +132,11 @@ int pir_reconstruct(const uint32_t* s0, const uint32_t* s1, size_t w, uint32_t* 
  * keys: host, batch * pir_key_bytes(n) bytes back to back, every key with
  * n == pir_domain_bits(t->rows).  out: batch x width words, host or device
  * (detected).  With a host `out` the call returns after the result is
- * there.  Errors: PIR_ERR_ARG, PIR_ERR_KEY, PIR_ERR_DOMAIN, PIR_ERR_NOMEM,
- * PIR_ERR_CUDA, PIR_ERR_UNSUPPORTED. */
+ * there.  Keys (and host-bound shares) are staged in stream-ordered device
+ * memory from a pool the library creates per device, which keeps up to
+ * 256 MiB of freed staging mapped between calls.  Errors: PIR_ERR_ARG,
+ * PIR_ERR_KEY, PIR_ERR_DOMAIN, PIR_ERR_NOMEM, PIR_ERR_CUDA,
+ * PIR_ERR_UNSUPPORTED. */
 int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
 
 /* Same computation with keys and outputs already in device memory (the
@@ -305,6 +311,7 @@ void pir_server_destroy(pir_server* server);
 
 #define PIR_CONTRACT_IMAD 0   /* CUDA-core 32-bit multiply-add */
 #define PIR_CONTRACT_MMA_U8 1 /* tensor-core u8 x u8 -> s32 MMAs on 8-bit limbs (10 per u32 product), exact */
+#define PIR_CONTRACT_SCAN 2   /* streaming table scan for a few queries, bound by HBM bandwidth */
 
 /* Expansion only (the level-by-level strategy's output, Sec. 3.2.2): writes
  * the full share vectors dshares[q * ld + j] = Eval(k_q, j) for j < rows,
@@ -318,8 +325,17 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
 
 /* dout[q][w] = sum_{j < t->rows} dshares[q * ld + j] * T[j][w]  (mod 2^32),
  * the share-matrix x table product of Sec. 3.1 ("batched together as a
- * single matrix-matrix multiplication").  engine: PIR_CONTRACT_IMAD or
- * PIR_CONTRACT_MMA_U8 (same result bit for bit).
+ * single matrix-matrix multiplication").  engine (same result bit for bit):
+ *  - PIR_CONTRACT_IMAD: 64 x 64 output tiles on CUDA cores, any batch;
+ *  - PIR_CONTRACT_MMA_U8: the same tiles on the tensor pipe (8-bit limbs);
+ *  - PIR_CONTRACT_SCAN: for a few queries, where the product is bound by
+ *    reading the table (Sec. 3.2.4): the copy engine streams table rows and
+ *    share words through shared memory, eight queries per pass over the
+ *    table.  Needs dshares and t->data 16-byte aligned, ld, t->stride and
+ *    t->width multiples of 4 and t->stride <= 1024, else
+ *    PIR_ERR_UNSUPPORTED.  Its waits on the copies are bounded: one that
+ *    gives up leaves dout incomplete and sets PIR_FAULT_WAIT_TIMEOUT (see
+ *    pir_device_status).
  * dout (device, batch x width) is overwritten.  Asynchronous. */
 int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
                      int engine, void* stream);
@@ -338,6 +354,12 @@ int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
  * time per launch in *best_ms (optional). */
 int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
                  pir_plan* plan, float* best_ms);
+
+/* Library-wide device fault bits, set by a kernel whose bounded wait gave
+ * up (the kernel then returns early; its output is incomplete).  Reads the
+ * bits of the current device (synchronous) and clears them if `clear`. */
+#define PIR_FAULT_WAIT_TIMEOUT 1u
+int pir_device_status(uint32_t* flags, int clear);
 
 /* Human-readable name of an error code (static string). */
 const char* pir_error_string(int code);

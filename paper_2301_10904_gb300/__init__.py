@@ -109,6 +109,7 @@ def _load():
         "pir_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp,
                                         ctypes.POINTER(pir_plan), ctypes.POINTER(ctypes.c_float)]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
+        "pir_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
     }
@@ -251,6 +252,8 @@ def pir_server_eval_range(shard, row_lo: int, domain_rows: int, dkeys, batch: in
 
 PIR_CONTRACT_IMAD = 0
 PIR_CONTRACT_MMA_U8 = 1
+PIR_CONTRACT_SCAN = 2
+PIR_FAULT_WAIT_TIMEOUT = 1
 
 
 def pir_expand_materialise(rows: int, dkeys, batch: int, dshares, dstatus=None, stream=None):
@@ -267,6 +270,13 @@ def pir_contract_u32(dshares, batch: int, table, dout, engine: int = PIR_CONTRAC
     _check(_lib.pir_contract_u32(dshares.data_ptr(), dshares.stride(0), batch, ctypes.byref(tb), dout.data_ptr(),
                                  engine, _stream(stream)), "pir_contract_u32")
     return dout
+
+
+def pir_device_status(clear: bool = False) -> int:
+    """Library-wide device fault bits of the current device (PIR_FAULT_*)."""
+    flags = ctypes.c_uint32(0)
+    _check(_lib.pir_device_status(ctypes.byref(flags), int(clear)), "pir_device_status")
+    return flags.value
 
 
 def _tables_array(tables):

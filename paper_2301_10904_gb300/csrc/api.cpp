@@ -42,6 +42,40 @@ static bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ---- staging memory for the host-buffer entry points ---------------------
+// Stream-ordered allocations from a pool the library owns (one per device).
+// The pool keeps up to kStagingKeepBytes of freed blocks mapped across stream
+// synchronisations; the device's default pool would hand them back to the
+// driver at every synchronisation and map them again on the next call.
+constexpr uint64_t kStagingKeepBytes = 256ull << 20;
+constexpr int kMaxDevices = 64;
+
+static int staging_pool(cudaMemPool_t* pool) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "get device");
+    if (dev < 0 || dev >= kMaxDevices) return PIR_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        CUDA_TRY(cudaMemPoolCreate(&p, &props), "create staging pool");
+        uint64_t keep = kStagingKeepBytes;
+        cudaError_t e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return cuda_fail((int)e, "staging pool threshold");
+        }
+        pools[dev] = p;
+    }
+    *pool = pools[dev];
+    return PIR_OK;
+}
+
 // ---- autotuned launch shapes --------------------------------------------
 // Keyed by (device, rows, width, batch rounded up to a power of two, whether
 // 128-bit loads apply); filled by pir_autotune, read by every evaluation.
@@ -246,6 +280,11 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
     return launch_materialise(req, plan, dshares, ld, stream);
 }
 
+int pir_device_status(uint32_t* flags, int clear) {
+    if (!flags) return PIR_ERR_ARG;
+    return pir::device_faults(flags, clear != 0);
+}
+
 int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
                      int engine, void* stream) {
     using namespace pir;
@@ -274,10 +313,12 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
     const size_t out_bytes = batch * (size_t)t->width * sizeof(uint32_t);
     uint8_t* dkeys = nullptr;
     uint32_t* dout = nullptr;
-    CUDA_TRY(cudaMallocAsync((void**)&dkeys, batch * kb, s), "alloc keys");
-    int rc = PIR_OK;
+    cudaMemPool_t pool = nullptr;
+    int rc = staging_pool(&pool);
+    if (rc != PIR_OK) return rc;
+    CUDA_TRY(cudaMallocFromPoolAsync((void**)&dkeys, batch * kb, pool, s), "alloc keys");
     if (!out_on_device) {
-        cudaError_t e = cudaMallocAsync((void**)&dout, out_bytes, s);
+        cudaError_t e = cudaMallocFromPoolAsync((void**)&dout, out_bytes, pool, s);
         if (e != cudaSuccess) {
             cudaFreeAsync(dkeys, s);
             return cuda_fail((int)e, "alloc shares");

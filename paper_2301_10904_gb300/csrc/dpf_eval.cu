@@ -23,11 +23,12 @@
 //     share their first two rounds' lookups); for leaves only the 5 output
 //     bytes that the share needs are computed in the last round.
 //  5. warp-specialised fusion (Sec. 3.2.4): 16 producer warps run steps 2-4
-//     and drop every kPairs leaf pairs' shares into one of two shared-memory
-//     buffers; 8 consumer warps multiply each buffer, for all G queries at
-//     once, into register accumulators against the table rows it indexes
-//     (each row read once per CTA), while the producers fill the other
-//     buffer.  Named barriers pass the buffers back and forth.
+//     and drop every kc (<= kPairs) leaf pairs' shares into one of two
+//     shared-memory buffers; 8 consumer warps multiply each buffer, for all
+//     G queries at once, into register accumulators against the table rows
+//     it indexes (each row read once per CTA), while the producers fill the
+//     other buffer.  Named barriers pass the buffers back and forth; the
+//     consumers have the copy engine prefetch the next phase's rows into L2.
 //  6. accumulators are summed in shared memory and added to out with one
 //     u32 atomicAdd per (query, word); addition mod 2^32 is associative, so
 //     the result is bit-exact in any order.
@@ -74,8 +75,16 @@ constexpr int kSmemBytes = kItemOff + 16;
 static_assert(kSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
 
 // The kernel's only shared memory; naming the array (not a pointer to it) in
-// every access lets the compiler address it as shared with an immediate base.
+// every access lets the compiler address it as shared.
 extern __shared__ __align__(128) char sm[];
+
+// Offset of `sm` in the CTA's shared window: the window begins with the 1 KiB
+// the system reserves per block (cudaDevAttrReservedSharedMemoryPerBlock), and
+// these kernels declare no static shared memory.  The table lookups carry it
+// as an immediate, so that a lookup is PRMT + LDS [reg + imm] with no address
+// add; the host refuses a device that reserves another amount and every
+// kernel checks the offset before its first lookup.
+constexpr uint32_t kSmemBase = 1024;
 
 struct FusedParams {
     const uint32_t* table;
@@ -137,15 +146,28 @@ __device__ uint32_t sbox_entry(uint32_t x) {
 // ---------------------------------------------------------------- lookups
 // Te_t[x] for this lane sits at plane(t)*64K + x*256 + (t&1)*128 + 4*lane:
 // one PRMT builds (x << 8) | (lane base), the plane offset is an immediate.
-#define LKT(s, r, t)                                                                      \
-    (*reinterpret_cast<const uint32_t*>(sm + ((t) >> 1) * kPlaneBytes +                 \
-                                        __byte_perm((s), ((t) & 1) ? lane4h : lane4, 0x5504u | ((r) << 4))))
+template <uint32_t OFF>
+__device__ __forceinline__ uint32_t lds_at(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+#define LKT(s, r, t) \
+    lds_at<kSmemBase + ((t) >> 1) * kPlaneBytes>(__byte_perm((s), ((t) & 1) ? lane4h : lane4, 0x5504u | ((r) << 4)))
 // main rounds: byte r of a column goes through Te_r
 #define LK(s, r) LKT(s, r, r)
 // S-box byte S(x) sits at byte p of Te_{(p+2)&3}[x]; gather four (one per byte position)
 #define SBG(a, b, c, d) __byte_perm(__byte_perm((a), (b), 0x0050u), __byte_perm((c), (d), 0x7200u), 0x7610u)
 // SubBytes+ShiftRows column: byte p from byte p of column (c+p)
 #define SBCOL(w0, w1, w2, w3) SBG(LKT(w0, 0, 2), LKT(w1, 1, 3), LKT(w2, 2, 0), LKT(w3, 3, 1))
+
+// Whether `sm` sits at kSmemBase of the shared window (uniform over the CTA,
+// so a CTA that finds otherwise returns as a whole, before any barrier).
+__device__ __forceinline__ bool smem_base_ok(uint32_t* status) {
+    if ((uint32_t)__cvta_generic_to_shared(sm) == kSmemBase) return true;
+    if (threadIdx.x == 0 && status) atomicOr(status, PIR_STATUS_SMEM_LAYOUT);
+    return false;
+}
 
 __device__ void build_tables(int tid) {
     uint32_t* stage = reinterpret_cast<uint32_t*>(sm + kStackOff);  // Te0 staged in the stack area
@@ -253,19 +275,41 @@ __device__ __forceinline__ void prf2_chacha(const uint4 v, uint4& c0, uint4& c1)
 
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
 
-// Children of v at depth d (1-based) of `key`: PRF plus C_{lsb(v)}[b][d].
-// `chacha` selects the key's PRF (uniform per query, so per warp in the DFS).
-__device__ __forceinline__ void expand(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
-                                       bool leaf, bool chacha, uint4& c0, uint4& c1) {
-    // the codewords' address is known before the PRF: issue the loads first
-    const uint4* cw = reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) + 32u * (v.x & 1u));
-    const uint4 w0 = __ldg(cw), w1 = __ldg(cw + 1);
+// Children of v: PRF plus the codeword pair C_{lsb(v)}[0][d], C_{lsb(v)}[1][d]
+// (w0, w1).  `chacha` selects the key's PRF (uniform per query, so per warp in
+// the DFS).
+__device__ __forceinline__ void expand_with(uint32_t lane4, uint32_t lane4h, uint4 v, bool leaf, bool chacha, uint4 w0,
+                                            uint4 w1, uint4& c0, uint4& c1) {
     if (chacha)
         prf2_chacha(v, c0, c1);
     else
         prf2(lane4, lane4h, v, leaf, c0, c1);
     c0 = xor4(c0, w0);
     c1 = xor4(c1, w1);
+}
+
+// Children of v at depth d (1-based) of `key` in global memory.
+__device__ __forceinline__ void expand(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
+                                       bool leaf, bool chacha, uint4& c0, uint4& c1) {
+    // the codewords' address is known before the PRF: issue the loads first
+    const uint4* cw = reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) + 32u * (v.x & 1u));
+    const uint4 w0 = __ldg(cw), w1 = __ldg(cw + 1);
+    expand_with(lane4, lane4h, v, leaf, chacha, w0, w1, c0, c1);
+}
+
+// Before the depth-first phase the stack region holds a copy of each query
+// slot's key (kKeySlotBytes apart), so that the path walk and the split, one
+// dependent level after another, read their codewords from shared memory.
+constexpr int kKeySlotBytes = PIR_KEY_HEADER_BYTES + 64 * PIR_MAX_DOMAIN_BITS;
+static_assert(kMaxGroup * kKeySlotBytes <= kStackBytes, "staged keys exceed the stack region");
+static_assert(kKeySlotBytes % 16 == 0, "key slots must keep 16-byte alignment");
+__device__ __forceinline__ const uint4* staged_key(int g) {
+    return reinterpret_cast<const uint4*>(sm + kStackOff + g * kKeySlotBytes);
+}
+__device__ __forceinline__ void expand_staged(uint32_t lane4, uint32_t lane4h, int g, uint32_t d, uint4 v, bool chacha,
+                                              uint4& c0, uint4& c1) {
+    const uint4* cw = staged_key(g) + (PIR_KEY_HEADER_BYTES / 16) + 4u * (d - 1) + 2u * (v.x & 1u);
+    expand_with(lane4, lane4h, v, false, chacha, cw[0], cw[1], c0, c1);
 }
 
 // Pending right sibling at relative level `lvl` (1..8) of thread `tid`.
@@ -283,6 +327,32 @@ __device__ __forceinline__ void load_row(const uint32_t* p, uint32_t (&v)[VEC]) 
     }
 }
 
+// Bulk prefetch of a byte range into L2 by the copy engine (no registers, no
+// shared memory; completes on its own).  addr 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* addr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr), "r"(bytes) : "memory");
+}
+
+// Table rows that one hand-off phase multiplies, per CTA, above which the
+// next phase is not prefetched (all CTAs' two phases in flight must fit L2).
+constexpr uint32_t kPrefetchMaxBytes = 256u * 1024u;
+
+// Consumers ask L2 for the rows of leaf pairs kbase..kbase+kc-1 of every
+// subtree ahead of the phase that multiplies them: per subtree one run of 2kc
+// consecutive rows, clipped to the table (16-byte rows only, VEC == 4).
+__device__ __forceinline__ void prefetch_phase(const FusedParams& p, uint64_t r0, int m, uint32_t nsub, uint32_t kbase,
+                                               uint32_t kc, uint32_t ct) {
+    for (uint32_t l = ct; l < nsub; l += kConsumers) {
+        uint64_t a = r0 + ((uint64_t)l << m) + 2ull * kbase, b = a + 2ull * kc;
+        a = a > p.row_lo ? a : p.row_lo;
+        b = b < p.row_hi ? b : p.row_hi;
+        if (a >= b) continue;
+        const uint64_t bytes = ((b - a - 1) * p.stride + p.width) * 4ull;
+        prefetch_l2(p.table + (a - p.row_lo) * p.stride, (uint32_t)bytes);
+    }
+}
+
 // Named barriers between producers and consumers: kBarFull + b marks share
 // buffer b as filled, kBarFree + b as consumed (barrier 0 is __syncthreads).
 constexpr int kBarFull = 1, kBarFree = 3;
@@ -296,7 +366,8 @@ __device__ __forceinline__ void bar_sync(int id, int count) {
 // Consumer thread `ct` of kConsumers: multiply the shares of leaf pairs
 // kbase..kbase+kc-1 of every subtree (buffer yb) into acc.  Consumer (c, rg)
 // owns words c*VEC..c*VEC+VEC-1 of every G query for rows rg, rg+nrg, ...;
-// four rows' loads are issued before their multiply-adds.
+// U rows' loads are issued before their multiply-adds (U = 8 for one or two
+// queries per item, where the scan is a large share of the work, else 4).
 template <int G, int VEC>
 __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* yb, uint64_t r0, int m, int sd,
                                           uint32_t kbase, uint32_t kc, uint32_t (&acc)[G][VEC], uint32_t ct) {
@@ -307,12 +378,13 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
     if (rg >= nrg) return;
     const uint32_t nrows = (2u * kc) << sd;
     const uint32_t submask = (1u << sd) - 1u;
-    for (uint32_t rr0 = rg; rr0 < nrows; rr0 += 4 * nrg) {
-        uint32_t tv[4][VEC];
-        uint32_t yi[4];
-        bool ok[4];
+    constexpr int U = G <= 2 ? 8 : 4;
+    for (uint32_t rr0 = rg; rr0 < nrows; rr0 += U * nrg) {
+        uint32_t tv[U][VEC];
+        uint32_t yi[U];
+        bool ok[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint32_t rr = rr0 + u * nrg;
             const uint32_t j = rr >> sd, l = rr & submask;
             const uint64_t row = r0 + ((uint64_t)l << m) + 2ull * kbase + j;
@@ -326,7 +398,7 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (!ok[u]) continue;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -383,6 +455,19 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     const int sd = min(LOG_SQ, r - 1);
     const int m = r - sd;
 
+    // ---- stage the group's keys in shared memory ---------------------------
+    {
+        const uint32_t kw = p.key_bytes / 16u;  // key length in 16-byte words
+        for (uint32_t i = tid; i < (uint32_t)G * kw; i += NT) {
+            const uint32_t g = i / kw, w = i - g * kw;
+            const uint8_t* key = hdr_slot((int)g)->key;
+            if (key)
+                reinterpret_cast<uint4*>(sm + kStackOff + g * kKeySlotBytes)[w] =
+                    __ldg(reinterpret_cast<const uint4*>(key) + w);
+        }
+    }
+    __syncthreads();
+
     // ---- key headers and the path to this item's range node ---------------
     uint4* bufA = reinterpret_cast<uint4*>(ybuf);
     uint4* bufB = bufA + kProducers;
@@ -391,19 +476,18 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         uint32_t ok = 0, party = 0, cwo = 0, prf = 0;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (h->key) {
-            const uint8_t* key = h->key;
-            const uint4 hw = __ldg(reinterpret_cast<const uint4*>(key));
+            const uint4 hw = staged_key(tid)[0];
             ok = hw.x == kKeyMagic && (hw.y & 0xffu) == kKeyVersion && ((hw.y >> 8) & 0xffu) == p.n &&
                  ((hw.y >> 16) & 0xffu) <= 1u && (hw.y >> 24) <= PIR_PRF_CHACHA20;
             if (ok) {
                 party = (hw.y >> 16) & 1u;
                 prf = hw.y >> 24;
                 cwo = hw.z;
-                v = __ldg(reinterpret_cast<const uint4*>(key + 16));
+                v = staged_key(tid)[1];
                 for (int d = 1; d <= n - r; ++d) {
                     const uint32_t b = (uint32_t)(r0 >> (n - d)) & 1u;
                     uint4 c0, c1;
-                    expand(lane4, lane4h, key, (uint32_t)d, v, false, prf != 0, c0, c1);
+                    expand_staged(lane4, lane4h, tid, (uint32_t)d, v, prf != 0, c0, c1);
                     v = b ? c1 : c0;
                 }
             } else if (p.status) {
@@ -427,7 +511,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
             const uint4 v = src[tid];
             uint4 c0 = v, c1 = v;
             const QueryHdr* h = hdr_slot(g);
-            if (h->ok) expand(lane4, lane4h, h->key, (uint32_t)(n - r + i + 1), v, false, h->prf != 0, c0, c1);
+            if (h->ok) expand_staged(lane4, lane4h, g, (uint32_t)(n - r + i + 1), v, h->prf != 0, c0, c1);
             dst[(g << (i + 1)) + 2 * idx] = c0;
             dst[(g << (i + 1)) + 2 * idx + 1] = c1;
         }
@@ -435,7 +519,21 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     }
     const int nsub = 1 << sd;
     const uint32_t npairs = 1u << (m - 1);
-    const uint32_t kc = npairs < (uint32_t)kPairs ? npairs : (uint32_t)kPairs;
+    // leaf pairs per hand-off: at most kPairs, and small enough that an item has
+    // four phases where it can, so that the scan of one phase overlaps the
+    // expansion of the next even when an item is small
+    uint32_t kc = max(1u, min((uint32_t)kPairs, npairs >> 2));
+    // With one or two queries per item the table scan weighs as much as the
+    // expansion: the consumers then have the copy engine prefetch the next
+    // phase's rows into L2, with phases small enough that two of every CTA's
+    // fit there.  (With more queries per item the rows are reused G times and
+    // the prefetch only costs issue slots.)
+    bool pf = false;
+    if constexpr (G <= 2 && VEC == 4 && !MAT) {
+        const uint64_t pair_bytes = (uint64_t)nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
+        while (kc > 1 && pair_bytes * kc > kPrefetchMaxBytes) kc >>= 1;
+        pf = pair_bytes * kc <= kPrefetchMaxBytes;
+    }
     const uint32_t nphases = npairs / kc;
     const int g = producer ? tid / SQ : 0, l = producer ? tid % SQ : 0;
     const QueryHdr* hq = hdr_slot(g);
@@ -503,7 +601,9 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     } else if constexpr (!MAT) {
         // ---- consumers: multiply every filled buffer into the accumulators ----
         const uint32_t ct = (uint32_t)(tid - kProducers);
+        if (pf) prefetch_phase(p, r0, m, (uint32_t)nsub, 0, kc, ct);
         for (uint32_t ph = 0; ph < nphases; ++ph) {
+            if (pf && ph + 1 < nphases) prefetch_phase(p, r0, m, (uint32_t)nsub, (ph + 1) * kc, kc, ct);
             bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
             mac_phase<G, VEC>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
             if (ph + 2 < nphases) bar_arrive(kBarFree + (int)(ph & 1u), kFusedThreads);
@@ -543,6 +643,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
 // that items running at the same time share table rows through L2.
 template <int G, int VEC, bool MAT>
 __device__ __forceinline__ void eval_items(const FusedParams& p) {
+    if (!smem_base_ok(p.status)) return;
     build_tables(threadIdx.x);
     for (uint64_t item = blockIdx.x; item < p.nitems; item += gridDim.x) {
         const uint32_t qg = (uint32_t)(item % p.nqg);
@@ -577,6 +678,7 @@ __global__ void __launch_bounds__(kProducers, 1) expand_materialise_kernel(const
 // from a counter, so uneven items balance themselves.
 template <int VEC>
 __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const MultiParams mp) {
+    if (!smem_base_ok(mp.status)) return;
     build_tables(threadIdx.x);
     uint64_t* s_item = reinterpret_cast<uint64_t*>(sm + kItemOff);
     for (;;) {
@@ -619,6 +721,20 @@ cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, int th
 }  // namespace dev
 
 // ------------------------------------------------------------------ host side
+
+// The lookups' immediate offsets assume the shared window reserves kSmemBase
+// bytes per block ahead of the kernel's own shared memory.
+static bool reserved_smem_ok() {
+    static int cached[64] = {};  // 0 unknown, 1 ok, 2 not
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!cached[dev]) {
+        int r = -1;
+        if (cudaDeviceGetAttribute(&r, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) return false;
+        cached[dev] = r == (int)dev::kSmemBase ? 1 : 2;
+    }
+    return cached[dev] == 1;
+}
 
 int device_sm_count() {
     int dev = 0, sms = 0;
@@ -667,10 +783,18 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     const int lsq = log_sq(g);
     int r = std::min((int)n, lsq + dev::kMaxDfsDepth);
     const int sms = std::max(1, device_sm_count());
-    // batches: shrink the items until there are about six per SM (balance of the last
-    // round); a few queries: about one item per SM (each item repeats the path walk)
-    const uint64_t target = (uint64_t)sms * (batch >= 8 ? 6 : 1);
-    while (r > std::min((int)n, lsq + 1) && items_for(row_lo, rows, (uint32_t)r, nqg) < target) --r;
+    const int r_min = std::min((int)n, lsq + 1);
+    if (batch >= 8) {
+        // batches: shrink the items until there are about six per SM (balance of the
+        // last round)
+        const uint64_t target = (uint64_t)sms * 6;
+        while (r > r_min && items_for(row_lo, rows, (uint32_t)r, nqg) < target) --r;
+    } else {
+        // a few queries: latency.  Every item walks n dependent levels (path, split,
+        // subtree), so give each CTA at most one item: the most items not above the
+        // SM count
+        while (r > r_min && items_for(row_lo, rows, (uint32_t)(r - 1), nqg) <= (uint64_t)sms) --r;
+    }
     pl.range_log2 = (uint32_t)r;
     const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
     pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
@@ -704,6 +828,7 @@ static uint32_t grid_for(uint64_t items) {
 }
 
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream) {
+    if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
     dev::FusedParams p = make_params(req, plan);
     p.shares = shares;
     p.ld = ld;
@@ -725,6 +850,7 @@ int multi_group() { return dev::kMaxGroup; }
 int multi_max_range_log2() { return log_sq(dev::kMaxGroup) + dev::kMaxDfsDepth; }
 
 int launch_multi(const MultiParams& mp, bool vec, void* stream) {
+    if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
     if (mp.nitems == 0) return PIR_OK;
     const uint32_t ctas = grid_for(mp.nitems);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -738,6 +864,7 @@ int launch_multi(const MultiParams& mp, bool vec, void* stream) {
 }
 
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
+    if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
     const dev::FusedParams p = make_params(req, plan);
     if (p.nitems == 0) return PIR_OK;
     const uint32_t ctas = grid_for(p.nitems);

@@ -95,6 +95,13 @@ int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* s
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                     uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream);
 
+// streaming scan engine for a few queries (scan.cu): eight queries per pass
+bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width);
+int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                uint32_t width, uint64_t rows, uint32_t* out, void* stream);
+// library-wide device fault bits (PIR_FAULT_*), read on the current device
+int device_faults(uint32_t* flags, bool clear);
+
 // error bookkeeping (api.cpp)
 int cuda_fail(int cuda_error_code, const char* what);
 

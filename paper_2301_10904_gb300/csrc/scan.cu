@@ -1,0 +1,251 @@
+// Share matrix x table mod 2^32 for a few queries: a streaming scan of the
+// table, bound by HBM bandwidth.  With a small batch the product of Sec. 3.1
+// ("batched together as a single matrix-matrix multiplication") does a few
+// multiply-adds per table byte, so every table row should leave HBM once, at
+// full bandwidth (Sec. 3.2.4: the table read is the memory-bound part).
+//
+//   out[b][w] += sum_{k < K} S[b][k] * T[k][w]   (mod 2^32),  b < B <= 8
+//
+// The copy engine streams chunks of R consecutive table rows, and the same R
+// share words of every query, into a ring of kScanStages shared-memory stages
+// (cp.async.bulk, completion counted in bytes on one mbarrier per stage);
+// 256 threads multiply each chunk into register accumulators while the next
+// stages are in flight.  Consumer (c, rg) owns words 4c..4c+3 for rows rg,
+// rg + nrg, ... of a chunk.  Partial sums meet in shared memory, then one u32
+// atomicAdd per (query, word) per CTA; addition mod 2^32 is associative, so
+// the result is bit-exact in any order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace pir {
+namespace dev {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanStages = 4;
+constexpr uint32_t kScanTableStageBytes = 16384;  // table bytes per stage (target)
+constexpr uint32_t kScanMaxRows = 512;            // rows per chunk cap (bounds the share slots)
+constexpr uint32_t kScanMaxWidth = 1024;          // words per row (R >= 4 keeps stages <= 16 KiB)
+constexpr uint32_t kScanHeader = 128;             // mbarriers + the wait verdict
+constexpr uint32_t kScanSpinLimit = 1u << 22;     // bounded waits (each try_wait may also suspend)
+
+// Set (bitwise) when a wait in one of the library's kernels gave up; read and
+// cleared by pir_device_status.
+__device__ uint32_t g_device_faults;
+
+struct ScanParams {
+    const uint32_t* S;
+    uint64_t ld;
+    const uint32_t* T;
+    uint64_t stride;
+    uint64_t K;
+    uint64_t nchunks;
+    uint32_t* out;
+    uint32_t B, W;
+    uint32_t R;            // rows per chunk, multiple of 4
+    uint32_t stage_bytes;  // R * stride * 4 (table slot) + 8 * R * 4 (share slots)
+};
+
+extern __shared__ __align__(128) char scan_sm[];
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kScanSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Thread 0: start the copies of chunk c into stage s.  Table rows
+// [k0, k0 + nr) as one run of (nr - 1) * stride + W words; for every query the
+// first nr & ~3 share words (the rest of a ragged last chunk is read by the
+// consumers directly).
+__device__ __forceinline__ void scan_issue(const ScanParams& p, uint32_t s, uint64_t c) {
+    const uint64_t k0 = c * p.R;
+    const uint32_t nr = (uint32_t)(p.K - k0 < p.R ? p.K - k0 : p.R), nr4 = nr & ~3u;
+    const uint32_t tbytes = (uint32_t)(((uint64_t)(nr - 1) * p.stride + p.W) * 4u);
+    const uint32_t sbytes = nr4 * 4u;
+    const uint32_t bar = smem_addr(scan_sm) + 8u * s;
+    const uint32_t dst = smem_addr(scan_sm + kScanHeader) + s * p.stage_bytes;
+    mbar_expect_tx(bar, tbytes + p.B * sbytes);
+    bulk_g2s(dst, p.T + k0 * p.stride, tbytes, bar);
+    if (sbytes)
+        for (uint32_t b = 0; b < p.B; ++b)
+            bulk_g2s(dst + p.R * (uint32_t)p.stride * 4u + b * p.R * 4u, p.S + b * p.ld + k0, sbytes, bar);
+}
+
+template <int BQ>
+__global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanParams p) {
+    const uint32_t tid = threadIdx.x;
+    uint32_t* verdict = reinterpret_cast<uint32_t*>(scan_sm + 64);
+    const uint32_t bar0 = smem_addr(scan_sm);
+    if (tid == 0) {
+        for (int s = 0; s < kScanStages; ++s) mbar_init(bar0 + 8u * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const uint64_t G = gridDim.x;
+    if (tid == 0)
+        for (uint32_t s = 0; s < (uint32_t)kScanStages; ++s) {
+            const uint64_t c = blockIdx.x + s * G;
+            if (c < p.nchunks) scan_issue(p, s, c);
+        }
+
+    const uint32_t nc = p.W / 4, nrg = kScanThreads / nc;
+    const uint32_t cc = tid % nc, rg = tid / nc;
+    uint32_t acc[BQ][4];
+#pragma unroll
+    for (int b = 0; b < BQ; ++b)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[b][e] = 0;
+
+    bool failed = false;
+    uint64_t j = 0;
+    for (uint64_t c = blockIdx.x; c < p.nchunks; c += G, ++j) {
+        const uint32_t s = (uint32_t)(j % kScanStages), parity = (uint32_t)((j / kScanStages) & 1u);
+        if (tid == 0) *verdict = mbar_wait(bar0 + 8u * s, parity) ? 1u : 0u;
+        __syncthreads();
+        if (*verdict == 0u) {
+            failed = true;
+            break;
+        }
+        mbar_try_wait(bar0 + 8u * s, parity);  // completed: gives this thread the copies' data
+        const uint64_t k0 = c * p.R;
+        const uint32_t nr = (uint32_t)(p.K - k0 < p.R ? p.K - k0 : p.R), nr4 = nr & ~3u;
+        const char* stage = scan_sm + kScanHeader + s * p.stage_bytes;
+        const uint32_t* sS = reinterpret_cast<const uint32_t*>(stage + p.R * (uint32_t)p.stride * 4u);
+        if (rg < nrg) {
+            for (uint32_t i = rg; i < nr; i += nrg) {
+                const uint4 t = *reinterpret_cast<const uint4*>(stage + ((uint64_t)i * p.stride + 4u * cc) * 4u);
+#pragma unroll
+                for (int b = 0; b < BQ; ++b) {
+                    uint32_t y = 0;
+                    if ((uint32_t)b < p.B) y = i < nr4 ? sS[b * p.R + i] : __ldg(p.S + b * p.ld + k0 + i);
+                    acc[b][0] += y * t.x;
+                    acc[b][1] += y * t.y;
+                    acc[b][2] += y * t.z;
+                    acc[b][3] += y * t.w;
+                }
+            }
+        }
+        __syncthreads();  // stage s is consumed
+        if (tid == 0 && c + kScanStages * G < p.nchunks) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            scan_issue(p, s, c + kScanStages * G);
+        }
+    }
+    if (failed) {
+        // a copy never completed: record it, wait (bounded) for the copies this
+        // CTA still has in flight, and leave without touching out
+        if (tid == 0) {
+            atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
+            for (uint64_t jj = j; jj < j + kScanStages; ++jj) {
+                const uint64_t c = blockIdx.x + jj * G;
+                if (c >= p.nchunks) break;
+                mbar_wait(bar0 + 8u * (uint32_t)(jj % kScanStages), (uint32_t)((jj / kScanStages) & 1u));
+            }
+        }
+        return;
+    }
+
+    // ---- partial sums of all consumers, then one atomic per (query, word) ----
+    uint32_t* red = reinterpret_cast<uint32_t*>(scan_sm + kScanHeader);
+    for (uint32_t i = tid; i < p.B * p.W; i += kScanThreads) red[i] = 0;
+    __syncthreads();
+    if (rg < nrg) {
+#pragma unroll
+        for (int b = 0; b < BQ; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if ((uint32_t)b < p.B && acc[b][e]) atomicAdd(&red[b * p.W + 4u * cc + e], acc[b][e]);
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < p.B * p.W; i += kScanThreads)
+        if (red[i]) atomicAdd(p.out + i, red[i]);
+}
+
+}  // namespace dev
+
+bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width) {
+    return (reinterpret_cast<uintptr_t>(shares) & 15u) == 0 && ld % 4 == 0 &&
+           (reinterpret_cast<uintptr_t>(table) & 15u) == 0 && stride % 4 == 0 && width % 4 == 0 &&
+           stride <= dev::kScanMaxWidth;
+}
+
+int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                uint32_t width, uint64_t rows, uint32_t* out, void* stream) {
+    using namespace dev;
+    if (!scan_supported(shares, ld, table, stride, width)) return PIR_ERR_UNSUPPORTED;
+    uint32_t R = (uint32_t)(kScanTableStageBytes / (stride * 4u)) & ~3u;
+    R = std::min(kScanMaxRows, std::max(4u, R));
+    ScanParams p{};
+    p.ld = ld;
+    p.T = table;
+    p.stride = stride;
+    p.K = rows;
+    p.nchunks = (rows + R - 1) / R;
+    p.W = width;
+    p.R = R;
+    p.stage_bytes = R * (uint32_t)stride * 4u + 8u * R * 4u;
+    const size_t smem = kScanHeader + (size_t)kScanStages * p.stage_bytes;
+    const int sms = std::max(1, device_sm_count());
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // eight queries per pass; each pass streams the whole table once
+    for (uint32_t b0 = 0; b0 < batch; b0 += 8) {
+        p.B = std::min(8u, batch - b0);
+        p.S = shares + (uint64_t)b0 * ld;
+        p.out = out + (uint64_t)b0 * width;
+        void (*kern)(ScanParams) = p.B > 4 ? contract_scan_kernel<8>
+                                   : p.B > 2 ? contract_scan_kernel<4>
+                                   : p.B > 1 ? contract_scan_kernel<2>
+                                             : contract_scan_kernel<1>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanThreads, smem);
+        if (e != cudaSuccess) return cuda_fail((int)e, "scan setup");
+        const uint64_t ctas = std::min<uint64_t>(p.nchunks, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
+        kern<<<(uint32_t)ctas, kScanThreads, smem, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail((int)e, "scan launch");
+    }
+    return PIR_OK;
+}
+
+int device_faults(uint32_t* flags, bool clear) {
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, dev::g_device_faults, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail((int)e, "read device faults");
+    if (clear && v) {
+        const uint32_t zero = 0;
+        e = cudaMemcpyToSymbol(dev::g_device_faults, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_fail((int)e, "clear device faults");
+    }
+    *flags = v;
+    return PIR_OK;
+}
+
+}  // namespace pir
