@@ -48,6 +48,13 @@ WORKLOADS = {
     "serving": dict(seed=55, rows=None, width=None,
                     desc="serving: Poisson arrivals over 4 resident tables (2^18x64, 2^20x32, 2^22x32, 2^24x16 "
                          "words, 1,728 MiB), table uniform per query, continuous cross-table batching"),
+    "pbr_1m": dict(rows=1 << 20, width=64, bin_rows=1 << 10, seed=21,
+                   desc="partial batch retrieval: the 2^20-row x 64-word table (256 MiB) cut into 1024 bins of "
+                        "2^10 rows, one DPF query per bin per step (1024 per step), all bins in one launch"),
+    "serving_hotfull": dict(seed=57, rows=None, width=None,
+                            desc="hot/full split serving: a 2^22-row x 32-word full table (512 MiB) and its 2^18 most "
+                                 "popular rows as a hot table, Poisson requests of 10 Zipf(1.1) rows, each sent as "
+                                 "exactly 10 hot + 3 full queries"),
     "multi_table": dict(seed=33, rows=None, width=None,
                         desc="multi-table: 2048 queries Zipf(1.1) over 8 tables (2^16..2^22 rows, 16..128 words, "
                              "1,460 MiB), one graph-captured persistent launch per step"),
@@ -239,6 +246,22 @@ def profiled_traffic(workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def client_gen_rate(pir, n: int, count: int, prf: int):
+    """Client Gen throughput on the host (Sec. 3.1: Gen is O(log L), Eval O(L)):
+    key pairs per second for `count` keys, on one thread and on all of them."""
+    count = max(count, 64)
+    alphas = [(i * 2654435761) % (1 << n) for i in range(count)]
+    res = {"n": n, "keys": count, "prf": PRF_NAMES[prf]}
+    for label, threads in (("one_thread", 1), ("all_threads", os.cpu_count() or 1)):
+        pir.pir_keygen_batch(n, alphas[:8], None, prf=prf, seed=b"\x11" * 32, threads=threads)  # warm-up
+        t0 = time.perf_counter()
+        pir.pir_keygen_batch(n, alphas, None, prf=prf, seed=b"\x11" * 32, threads=threads)
+        dt = time.perf_counter() - t0
+        res[label] = {"key_pairs_per_s": round(count / dt, 1), "us_per_key_pair": round(1e6 * dt / count, 2),
+                      "threads": threads}
+    return res
+
+
 def _pack_keys(keys, offsets, total):
     buf = bytearray(total)
     for k, o in zip(keys, offsets):
@@ -352,6 +375,7 @@ class SingleTableWorkload:
             del S
         if self.args.scan and self.width % 4 == 0 and self.rows * self.width * 4 > 2 * L2_BYTES:
             out["scan"] = self.scan_roofline()
+        out["client_gen"] = client_gen_rate(self.pir, self.n, self.batch, self.prf)
         return out
 
     def scan_roofline(self):
@@ -620,8 +644,221 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving_hotfull(args):
+    """Hot/full table split (Sec. 4) on the serving loop: every request carries
+    exactly Q_hot hot-table and Q_full full-table queries; a request's latency
+    is that of its slowest query.  Compared with the same requests sent as
+    Q_hot + Q_full full-table queries (no split)."""
+    import torch
+
+    import __graft_entry__ as g
+
+    rank, local_rank, world = dist_env()
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    dist_init(world, "nccl")
+    g.build()
+    import paper_2301_10904_gb300 as pir
+
+    wk = WORKLOADS["serving_hotfull"]
+    seed = rank_seed(wk["seed"], rank)
+    full_rows, width = wl.HOTFULL_FULL
+    qh, qf, K = wl.HOTFULL_Q_HOT, wl.HOTFULL_Q_FULL, wl.HOTFULL_WANTED
+    q = qh + qf
+    z = wl.ZipfRows(seed, full_rows)
+    hot_rows = z.top(wl.HOTFULL_HOT_ROWS)
+    full = wl.table_u32_torch(seed * 100, full_rows, width, device)
+    hot = full[torch.from_numpy(hot_rows.astype(np.int64)).to(device)].contiguous()
+    srv = pir.Server(max_batch=2048, streams=2)
+    tid_hot, tid_full = srv.register_table(hot), srv.register_table(full)
+    rates = [int(x) for x in args.req_rates.split(",")]
+    R = max(min(int(r * args.seconds), args.max_requests // q) for r in rates)
+    wanted = z.sample(seed + 1, R * K).reshape(R, K)
+
+    def build(split: bool):
+        """Per request: keys of both parties, table ids and share offsets of its q queries."""
+        k0s, k1s, tids, slots = [], [], [], []
+        for r in range(R):
+            hk0, hk1, fk0, fk1, slot = pir.pir_hotfull_keygen(
+                full_rows, hot_rows, wanted[r], qh if split else 0, qf if split else q,
+                seed=hashlib.sha256(b"hotfull%d-%d-%d" % (seed, r, split)).digest())
+            nh = qh if split else 0
+            hkb = len(hk0) // nh if nh else 0
+            fkb = len(fk0) // (q - nh)
+            k0s += [hk0[i * hkb:(i + 1) * hkb] for i in range(nh)] + [fk0[i * fkb:(i + 1) * fkb] for i in range(q - nh)]
+            k1s += [hk1[i * hkb:(i + 1) * hkb] for i in range(nh)] + [fk1[i * fkb:(i + 1) * fkb] for i in range(q - nh)]
+            tids += [tid_hot] * nh + [tid_full] * (q - nh)
+            slots.append(slot)
+        klens = np.array([len(k) for k in k0s], np.uint64)
+        koff = np.concatenate([[0], np.cumsum(klens)[:-1]]).astype(np.uint64)
+        ooff = (np.arange(R * q, dtype=np.uint64) * width).astype(np.uint64)
+        return b"".join(k0s), b"".join(k1s), np.array(tids, np.uint32), koff, ooff, slots
+
+    plans = {True: build(True), False: build(False)}
+
+    def replay(split, rate, count, party=0):
+        keys0, keys1, tids, koff, ooff, _ = plans[split]
+        arr = np.repeat(wl.poisson_arrivals(seed + rate, rate, count), q)  # a request's queries arrive together
+        outs = np.zeros(count * q * width, np.uint32)
+        lat, el = srv.replay(arr, tids[:count * q], keys0 if party == 0 else keys1, koff[:count * q], outs,
+                             ooff[:count * q])
+        return lat.reshape(count, q).max(axis=1) / 1e6, el, outs
+
+    replay(True, 200, min(50, R))  # warm-up: lookup tables, batch buffers
+    # correctness: both servers over the first requests reconstruct every kept row
+    nchk = min(64, R)
+    ok = True
+    for split in (True, False):
+        _, _, o0 = replay(split, 400, nchk, 0)
+        _, _, o1 = replay(split, 400, nchk, 1)
+        rec = ((o0.astype(np.uint64) + o1) & 0xFFFFFFFF).astype(np.uint32).reshape(nchk, q, width)
+        for r in range(nchk):
+            for i, sl in enumerate(plans[split][5][r]):
+                if sl >= 0:
+                    ok = ok and np.array_equal(rec[r, sl], full[int(wanted[r, i])].cpu().numpy().view(np.uint32))
+    drop = {s: float(np.mean([np.mean(np.asarray(x) < 0) for x in plans[s][5]])) for s in (True, False)}
+
+    results = {True: [], False: []}
+    sampler = ClockSampler(gpu_id_for(device) if rank == 0 else None)
+    barrier(world, device)
+    with sampler if rank == 0 else _Null():
+        for split in (True, False):
+            for rate in rates:
+                count = min(int(rate * args.seconds), R)
+                lat, el, _ = replay(split, rate, count)
+                results[split].append({"offered_rps": rate, "requests": count, "achieved_rps": round(count / el, 1),
+                                       "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                       "p99_ms": round(float(np.percentile(lat, 99)), 3)})
+    st = srv.stats()
+    srv.close()
+    if rank != 0:
+        return
+
+    def summary(res):
+        best = max(res, key=lambda r: r["achieved_rps"])
+        knee = max([r for r in res if r["achieved_rps"] >= 0.95 * r["offered_rps"]] or [res[0]],
+                   key=lambda r: r["offered_rps"])
+        return best, knee
+
+    best, knee = summary(results[True])
+    nbest, nknee = summary(results[False])
+    out = {
+        "metric": METRIC, "value": round(best["achieved_rps"] * q, 1), "unit": "queries/s", "n_gpus": world,
+        "steps": sum(r["requests"] for r in results[True]), "warmup": 50,
+        "ms_per_step": round(1e3 / best["achieved_rps"], 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded SplitMix64 table, Zipf(1.1) row popularity through a seeded permutation, "
+                "Poisson request arrivals, keys from pir_hotfull_keygen)",
+        "config": {"workload": wk["desc"], "full": {"rows": full_rows, "width_words": width},
+                   "hot": {"rows": int(hot_rows.size), "width_words": width}, "wanted_per_request": K,
+                   "q_hot": qh, "q_full": qf, "prf": "AES-128",
+                   "server": {"max_batch": 2048, "streams": 2, "max_inflight": st["max_inflight"]},
+                   "l2": "inputs larger than L2 (512 MiB full table), no flush",
+                   "parallelism": f"{world} replica(s), independent requests"},
+        "latency_ms": {"p50": knee["p50_ms"], "p99": knee["p99_ms"], "at_offered_rps": knee["offered_rps"]},
+        "requests_per_s": best["achieved_rps"],
+        "rates": results[True],
+        "dropped_fraction": round(drop[True], 5),
+        "no_split": {"q_full": q, "requests_per_s": nbest["achieved_rps"], "knee_offered_rps": nknee["offered_rps"],
+                     "p50_ms": nknee["p50_ms"], "p99_ms": nknee["p99_ms"], "rates": results[False],
+                     "dropped_fraction": round(drop[False], 5)},
+        "gpu_launches": st["batches"], "server_stats": st,
+        "e2e": {"value": round(best["achieved_rps"] * q, 1), "unit": "queries/s",
+                "h2d_bytes_per_step": int(len(plans[True][0]) // R), "d2h_bytes_per_step": q * width * 4,
+                "note": "the serving loop is end to end: host keys in, host shares out; per request"},
+        "selfcheck_reconstruct_all": ok, "clocks": sampler.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
+class PbrWorkload:
+    """Partial batch retrieval (Sec. 4, batch PIR): one table cut into bins, one
+    DPF query over each bin per step (pir_pbr_keygen on the client side), every
+    bin in one launch (pir_server_eval_pbr).  A query here is one bin's query."""
+
+    def __init__(self, name, wk, pir, torch, device, stream, seed, args):
+        self.name, self.pir, self.torch, self.device, self.stream, self.args = name, pir, torch, device, stream, args
+        self.rows, self.width, self.bin_rows = wk["rows"], wk["width"], wk["bin_rows"]
+        self.desc, self.seed = wk["desc"], seed
+        self.prf = PRFS[args.prf]
+        self.nbins = -(-self.rows // self.bin_rows)
+        self.nb = pir.pir_domain_bits(self.bin_rows)
+        self.table = wl.table_u32_torch(seed, self.rows, self.width, device)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.wanted = rng.integers(0, self.rows, self.nbins)  # as many wanted rows as bins: some collide
+        k0, k1, self.kept = pir.pir_pbr_keygen(self.rows, self.bin_rows, self.wanted, prf=self.prf,
+                                               seed=hashlib.sha256(b"pbr%d" % seed).digest())
+        self.keys1 = k1
+        self.dkeys = torch.frombuffer(bytearray(k0), dtype=torch.uint8).to(device)
+        self.dout = torch.empty((self.nbins, self.width), dtype=torch.int32, device=device)
+        self.hkeys = torch.frombuffer(bytearray(k0), dtype=torch.uint8).pin_memory()
+        self.hout = torch.empty((self.nbins, self.width), dtype=torch.int32).pin_memory()
+        self.dkeys_e2e = torch.empty_like(self.dkeys)
+        self.dout_e2e = torch.empty_like(self.dout)
+        self.queries_per_step = self.nbins
+        self.nodes_per_step = self.nbins * ((1 << self.nb) - 1)
+        self.kernel = "bins_eval_kernel"
+        self.h2d_bytes, self.d2h_bytes = len(k0), self.nbins * self.width * 4
+
+    def step(self):
+        self.pir.pir_server_eval_pbr(self.table, self.bin_rows, self.dkeys, self.dout, stream=self.stream)
+
+    def e2e_step(self):
+        # pinned host keys in, host shares out: the copies are inside the timed region
+        self.dkeys_e2e.copy_(self.hkeys, non_blocking=True)
+        self.pir.pir_server_eval_pbr(self.table, self.bin_rows, self.dkeys_e2e, self.dout_e2e, stream=self.stream)
+        self.hout.copy_(self.dout_e2e, non_blocking=True)
+
+    def e2e_matches(self):
+        self.torch.cuda.synchronize(self.device)
+        return bool(np.array_equal(self.hout.numpy(), self.dout.cpu().numpy()))
+
+    def selfcheck(self):
+        torch, pir = self.torch, self.pir
+        d1 = torch.empty_like(self.dout)
+        k1 = torch.frombuffer(bytearray(self.keys1), dtype=torch.uint8).to(self.device)
+        pir.pir_server_eval_pbr(self.table, self.bin_rows, k1, d1, stream=self.stream)
+        torch.cuda.synchronize(self.device)
+        rec = ((self.dout.cpu().numpy().view(np.uint32).astype(np.uint64) + d1.cpu().numpy().view(np.uint32))
+               & 0xFFFFFFFF).astype(np.uint32)
+        idx = np.asarray(self.wanted, dtype=np.int64)[self.kept]
+        want = self.table[torch.from_numpy(idx).to(self.device)].cpu().numpy().view(np.uint32)
+        claimed = np.zeros(self.nbins, bool)
+        claimed[idx // self.bin_rows] = True
+        return bool(np.array_equal(rec[idx // self.bin_rows], want) and not rec[~claimed].any())
+
+    def config(self):
+        return {"workload": self.desc, "rows": self.rows, "width_words": self.width, "bin_rows": self.bin_rows,
+                "bins": self.nbins, "n_per_bin": self.nb, "prf": PRF_NAMES[self.prf],
+                "l2": f"inputs larger than L2: table {self.rows * self.width * 4 >> 20} MiB per step, no flush"}
+
+    def extras(self):
+        return {"pbr": {"wanted_rows_per_step": int(len(self.wanted)), "retrieved_rows_per_step": int(self.kept.sum()),
+                        "dropped_fraction": round(1.0 - float(self.kept.sum()) / len(self.wanted), 4),
+                        "key_bytes_per_query": self.pir.pir_key_bytes(self.nb)}}
+
+    def cpu_baseline(self):
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+
+        oracle.build()
+        threads = os.cpu_count() or 1
+        T = self.table.cpu().numpy().view(np.uint32)
+        kb = self.pir.pir_key_bytes(self.nb)
+        keys = bytes(self.dkeys.cpu().numpy())
+        sample = list(range(0, self.nbins, max(1, self.nbins // (8 * threads))))
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda b: oracle.answer(keys[b * kb:(b + 1) * kb],
+                                                T[b * self.bin_rows:(b + 1) * self.bin_rows]), sample))
+        wall = time.perf_counter() - t0
+        return {"value": round(len(sample) / wall, 4), "unit": "queries/s", "cores": min(threads, len(sample)),
+                "kind": "oracle", "sample": f"{len(sample)} bin queries of this workload (oracle FullEval over the "
+                                            f"bin + inner product), {threads} host threads, {wall:.1f} s wall"}
+
+
 WORKLOAD_CLASSES = {"batched_1m": SingleTableWorkload, "plain_64k": SingleTableWorkload,
-                    "large_16m": SingleTableWorkload, "multi_table": MultiTableWorkload}
+                    "large_16m": SingleTableWorkload, "multi_table": MultiTableWorkload, "pbr_1m": PbrWorkload}
 
 
 def run_ours(args):
@@ -786,6 +1023,28 @@ def run_reference(args):
                 list(ex.map(lambda tk: oracle.answer(tk[1], tables[tk[0]]), keys))
             return len(qs) / (time.perf_counter() - t0), threads, len(qs), time.perf_counter() - t0
         rows = width = None
+    elif args.workload == "pbr_1m":
+        rows, width, bin_rows = wk["rows"], wk["width"], wk["bin_rows"]
+        table_np = wl.table_u32(wk["seed"], rows, width)
+        nb = wl.domain_bits(bin_rows)
+        nbins = -(-rows // bin_rows)
+
+        def one_step(i):
+            from concurrent.futures import ThreadPoolExecutor
+
+            import oracle
+
+            threads = os.cpu_count() or 1
+            bins = [(i * 16 * threads + j) % nbins for j in range(16 * threads)]
+            keys = []
+            for b in bins:
+                r0, r1, c0 = wl.key_randomness(wk["seed"] + b, nb, 1)[0]
+                keys.append((b, oracle.gen(nb, b % bin_rows, 1, r0, r1, c0)[0]))
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda bk: oracle.answer(bk[1], table_np[bk[0] * bin_rows:(bk[0] + 1) * bin_rows]),
+                            keys))
+            return len(bins) / (time.perf_counter() - t0), threads, len(bins), time.perf_counter() - t0
     else:
         rows, width = wk["rows"], wk["width"]
         table_np = wl.table_u32(wk["seed"], rows, width)
@@ -828,6 +1087,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rates", default="1000,2000,4000,6000,10000,20000,50000,100000,200000",
                     help="serving workload: offered Poisson rates (queries/s)")
+    ap.add_argument("--req-rates", default="100,200,400,800,1200,1600,2400,4000",
+                    help="hot/full serving workload: offered Poisson request rates (requests/s)")
     ap.add_argument("--seconds", type=float, default=1.0, help="serving workload: arrival span per rate")
     ap.add_argument("--max-requests", type=int, default=8000, help="serving workload: requests per rate, at most")
     ap.add_argument("--no-materialised", dest="materialised", action="store_false",
@@ -841,6 +1102,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "serving_hotfull":
+        run_serving_hotfull(args)
     else:
         run_ours(args)
 

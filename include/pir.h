@@ -116,6 +116,52 @@ int pir_keygen(uint32_t n, uint64_t alpha, uint32_t beta, const uint8_t* seed, u
 int pir_keygen_prf(uint32_t n, uint64_t alpha, uint32_t beta, uint32_t prf, const uint8_t* seed, uint8_t* key0,
                    uint8_t* key1);
 
+/* Many keys at once (the client's Gen for a batch of queries, Sec. 3.1):
+ * key pair i is pir_keygen_prf(n, alphas[i], betas ? betas[i] : 1, prf,
+ * seed_i), written at keys0/keys1 + i * pir_key_bytes(n) (host).  seed_i is
+ * the i-th 32-byte block of the AES-128-CTR stream of `seed` (32 bytes, or
+ * NULL: a master seed from the operating system's entropy source), so the
+ * keys do not depend on `threads` (0 = one per hardware thread).  Errors: as
+ * pir_keygen_prf, for the first failing key. */
+int pir_keygen_batch(uint32_t n, size_t count, const uint64_t* alphas, const uint32_t* betas, uint32_t prf,
+                     const uint8_t* seed, uint8_t* keys0, uint8_t* keys1, uint32_t threads);
+
+/* Partial batch retrieval, client side (Sec. 4, batch PIR after [multihot]):
+ * the table's `rows` rows are cut into nbins = ceil(rows / bin_rows) bins of
+ * bin_rows rows (the last may be shorter) and one query goes to every bin,
+ * a DPF over n_b = pir_domain_bits(bin_rows) levels.  Of the `count` wanted
+ * row indices, the first that falls in a bin is retrieved (kept[i] = 1,
+ * alpha = index - bin * bin_rows, beta = 1); a later one in the same bin is
+ * dropped (kept[i] = 0; a bin yields one entry).  Bins with no wanted index
+ * get a dummy query (alpha = 0, beta = 0), so neither server learns which bins
+ * were wanted.  keys0/keys1: nbins * pir_key_bytes(n_b) bytes each (host),
+ * generated as pir_keygen_batch with `seed`.  Errors: PIR_ERR_ARG (bin_rows <
+ * 2, null buffers), PIR_ERR_DOMAIN (an index >= rows). */
+int pir_pbr_keygen(uint64_t rows, uint64_t bin_rows, const uint64_t* indices, size_t count, uint32_t prf,
+                   const uint8_t* seed, uint8_t* keys0, uint8_t* keys1, uint8_t* kept);
+
+/* Frequency-based hot/full table split, client side (Sec. 4, "Frequency-Based
+ * Hot Table Split"): next to the full table (full_rows rows) the server holds a
+ * hot table of hot_count rows, hot row h being full-table row hot_rows[h]
+ * (hot_rows strictly increasing; the client's copy of this map is the paper's
+ * on-device index of hot entries).  Every request sends exactly q_hot queries
+ * to the hot table and q_full to the full table, so neither server learns how
+ * many wanted rows are hot or how many rows are wanted.  Wanted full-table
+ * rows, in order: a hot row goes to the hot table while hot queries remain;
+ * any other row, or a hot row once the hot queries are used, goes to the full
+ * table while full queries remain; the rest are dropped (slot[i] = -1).
+ * slot[i] = s for hot query s, q_hot + s for full query s.  Unused queries
+ * are dummies (alpha 0, beta 0).  Keys: hot keys over
+ * pir_domain_bits(hot_count) levels (q_hot key pairs back to back), full keys
+ * over pir_domain_bits(full_rows) levels, each set generated as
+ * pir_keygen_batch with a 32-byte seed drawn from `seed`'s AES-128-CTR stream
+ * (first block pair: hot, second: full; NULL: operating-system entropy).
+ * Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN (a wanted row >= full_rows). */
+int pir_hotfull_keygen(uint64_t full_rows, const uint64_t* hot_rows, uint64_t hot_count, const uint64_t* indices,
+                       size_t count, uint32_t q_hot, uint32_t q_full, uint32_t prf, const uint8_t* seed,
+                       uint8_t* hot_keys0, uint8_t* hot_keys1, uint8_t* full_keys0, uint8_t* full_keys1,
+                       int64_t* slot);
+
 /* Validates a key's header (magic, version, n, party, length == 32 + 64 n).
  * On success stores n and the party (0 or 1).  Errors: PIR_ERR_ARG,
  * PIR_ERR_KEY. */
@@ -306,6 +352,22 @@ int pir_server_replay(pir_server* server, const double* arrival_s, const uint32_
 
 /* Drains, stops the worker and frees the server's buffers. */
 void pir_server_destroy(pir_server* server);
+
+/* ---- partial batch retrieval, server side ---------------------------- */
+
+/* Sec. 4 (batch PIR, after [multihot]): key b is a DPF over bin b of the
+ * table, rows [b * bin_rows, min((b + 1) * bin_rows, t->rows)), and
+ *   dout[b][w] = sum_{j < rows of bin b} Eval(k_b, j) * T[b * bin_rows + j][w]   (mod 2^32)
+ * for b < nbins = ceil(t->rows / bin_rows).  One launch: every CTA work item
+ * holds up to 8 bins side by side (each with its own rows), so a bin of a
+ * few thousand rows still fills the GPU.  dkeys: device, nbins *
+ * pir_key_bytes(pir_domain_bits(bin_rows)) bytes, 16-byte aligned (as
+ * written by pir_pbr_keygen).  dout: device, nbins x width, overwritten.
+ * dstatus: as pir_server_eval_device.  Needs bin_rows >= 2, 16-byte aligned
+ * rows (t->data 16-byte aligned; stride and width multiples of 4) and width
+ * <= 1024, else PIR_ERR_ARG / PIR_ERR_UNSUPPORTED.  Asynchronous. */
+int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dkeys, uint32_t* dout,
+                        uint32_t* dstatus, void* stream);
 
 /* ---- materialised (unfused) baseline ------------------------------- */
 

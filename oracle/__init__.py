@@ -221,6 +221,58 @@ def contract(S: np.ndarray, T: np.ndarray) -> np.ndarray:
         return ((S @ T) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
 
 
+def pbr_plan(rows: int, bin_rows: int, indices):
+    """Partial batch retrieval, client side (Sec. 4, batch PIR): the table is
+    cut into ceil(rows / bin_rows) bins of bin_rows rows and every bin gets one
+    query.  A bin yields one entry: the first wanted index that falls in it is
+    retrieved, any later one in the same bin is dropped.  A bin nobody wants
+    gets a dummy query (alpha 0, beta 0).  Returns (alphas, betas, kept)."""
+    nbins = -(-rows // bin_rows)
+    alphas, betas, kept = [0] * nbins, [0] * nbins, []
+    for idx in indices:
+        b = int(idx) // bin_rows
+        if betas[b] == 0:
+            alphas[b], betas[b] = int(idx) - b * bin_rows, 1
+            kept.append(True)
+        else:
+            kept.append(False)
+    return alphas, betas, kept
+
+
+def pbr_answer(keys, table: np.ndarray, bin_rows: int) -> np.ndarray:
+    """Partial batch retrieval, server side: bin b's share is the answer of
+    key b over the bin's own rows, table[b * bin_rows : (b + 1) * bin_rows]."""
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    return np.stack([answer(k, table[b * bin_rows:(b + 1) * bin_rows]) for b, k in enumerate(keys)])
+
+
+def hotfull_plan(full_rows: int, hot_rows, indices, q_hot: int, q_full: int):
+    """Frequency-based hot/full split, client side (Sec. 4): exactly q_hot
+    queries to the hot table (hot row h = full row hot_rows[h]) and q_full to
+    the full table per request.  A wanted hot row uses a hot query while any
+    remain; other rows, and hot rows past the hot budget, use full queries
+    while any remain; the rest are dropped.  Unused queries are dummies
+    (alpha 0, beta 0).  Returns (hot_alphas, hot_betas, full_alphas,
+    full_betas, slots); slots[i] = s (hot query s), q_hot + s (full query s)
+    or -1 (dropped)."""
+    where = {int(r): h for h, r in enumerate(hot_rows)}
+    ha, hb, fa, fb, slots = [0] * q_hot, [0] * q_hot, [0] * q_full, [0] * q_full, []
+    nh = nf = 0
+    for idx in indices:
+        idx = int(idx)
+        if idx in where and nh < q_hot:
+            ha[nh], hb[nh] = where[idx], 1
+            slots.append(nh)
+            nh += 1
+        elif nf < q_full:
+            fa[nf], fb[nf] = idx, 1
+            slots.append(q_hot + nf)
+            nf += 1
+        else:
+            slots.append(-1)
+    return ha, hb, fa, fb, slots
+
+
 def reconstruct(s0: np.ndarray, s1: np.ndarray) -> np.ndarray:
     s0 = np.ascontiguousarray(s0, dtype=np.uint32)
     s1 = np.ascontiguousarray(s1, dtype=np.uint32)

@@ -19,6 +19,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libpir.so")
 
 PIR_OK = 0
 PIR_STATUS_BAD_KEY = 1
+PIR_STATUS_SMEM_LAYOUT = 2
 ERRORS = {-1: "PIR_ERR_ARG", -2: "PIR_ERR_DOMAIN", -3: "PIR_ERR_KEY", -4: "PIR_ERR_NOMEM", -5: "PIR_ERR_CUDA",
           -6: "PIR_ERR_TIMEOUT", -7: "PIR_ERR_BUSY", -8: "PIR_ERR_UNSUPPORTED"}
 
@@ -70,6 +71,14 @@ def _load():
         "pir_keygen": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, u8p, u8p, u8p]),
         "pir_keygen_prf": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p,
                                           u8p, u8p]),
+        "pir_keygen_batch": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_size_t, vp, vp, ctypes.c_uint32, u8p, u8p, u8p,
+                                            ctypes.c_uint32]),
+        "pir_pbr_keygen": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, vp, ctypes.c_size_t, ctypes.c_uint32, u8p,
+                                          u8p, u8p, vp]),
+        "pir_server_eval_pbr": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_uint64, u8p, u32p, u32p, vp]),
+        "pir_hotfull_keygen": (ctypes.c_int, [ctypes.c_uint64, vp, ctypes.c_uint64, vp, ctypes.c_size_t,
+                                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u8p, u8p, u8p, u8p,
+                                              u8p, vp]),
         "pir_key_check": (ctypes.c_int, [u8p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint32),
                                          ctypes.POINTER(ctypes.c_uint32)]),
         "pir_reconstruct": (ctypes.c_int, [u32p, u32p, ctypes.c_size_t, u32p]),
@@ -176,6 +185,67 @@ def pir_keygen_prf(n: int, alpha: int, beta: int = 1, prf: int = PIR_PRF_AES128,
     return k0.raw, k1.raw
 
 
+def pir_keygen_batch(n: int, alphas, betas=None, prf: int = PIR_PRF_AES128, seed: bytes | None = None,
+                     threads: int = 0):
+    """count key pairs at once; returns (keys0, keys1) as bytes, keys back to back."""
+    import numpy as np
+
+    a = np.ascontiguousarray(alphas, dtype=np.uint64)
+    b = None if betas is None else np.ascontiguousarray(np.asarray(betas, dtype=np.uint64) & 0xFFFFFFFF,
+                                                        dtype=np.uint32)
+    if seed is not None and len(seed) != 32:
+        raise ValueError("seed must be 32 bytes")
+    kb = pir_key_bytes(n) * a.size
+    k0 = ctypes.create_string_buffer(max(1, kb))
+    k1 = ctypes.create_string_buffer(max(1, kb))
+    _check(_lib.pir_keygen_batch(n, a.size, a.ctypes.data, b.ctypes.data if b is not None else None, prf,
+                                 _buf(seed) if seed is not None else None, ctypes.cast(k0, ctypes.c_void_p),
+                                 ctypes.cast(k1, ctypes.c_void_p), threads), "pir_keygen_batch")
+    return k0.raw[:kb], k1.raw[:kb]
+
+
+def pir_pbr_keygen(rows: int, bin_rows: int, indices, prf: int = PIR_PRF_AES128, seed: bytes | None = None):
+    """Partial batch retrieval, client side: one key pair per bin.  Returns
+    (keys0, keys1, kept) with kept[i] true when indices[i] is retrieved."""
+    import numpy as np
+
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    nbins = (rows + bin_rows - 1) // bin_rows if bin_rows else 0
+    kb = pir_key_bytes(pir_domain_bits(bin_rows)) * nbins if bin_rows >= 2 else 0
+    k0 = ctypes.create_string_buffer(max(1, kb))
+    k1 = ctypes.create_string_buffer(max(1, kb))
+    kept = np.zeros(max(1, idx.size), dtype=np.uint8)
+    if seed is not None and len(seed) != 32:
+        raise ValueError("seed must be 32 bytes")
+    _check(_lib.pir_pbr_keygen(rows, bin_rows, idx.ctypes.data if idx.size else None, idx.size, prf,
+                               _buf(seed) if seed is not None else None, ctypes.cast(k0, ctypes.c_void_p),
+                               ctypes.cast(k1, ctypes.c_void_p), kept.ctypes.data), "pir_pbr_keygen")
+    return k0.raw[:kb], k1.raw[:kb], kept[:idx.size].astype(bool)
+
+
+def pir_hotfull_keygen(full_rows: int, hot_rows, indices, q_hot: int, q_full: int, prf: int = PIR_PRF_AES128,
+                       seed: bytes | None = None):
+    """Hot/full table split, client side: exactly q_hot hot-table and q_full
+    full-table key pairs.  Returns (hot_keys0, hot_keys1, full_keys0,
+    full_keys1, slot) with slot[i] the query that carries indices[i] (hot
+    queries first), or -1 when it was dropped."""
+    import numpy as np
+
+    hot = np.ascontiguousarray(hot_rows, dtype=np.uint64)
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    hkb = pir_key_bytes(pir_domain_bits(hot.size)) * q_hot if hot.size >= 2 else 0
+    fkb = pir_key_bytes(pir_domain_bits(full_rows)) * q_full if full_rows >= 2 else 0
+    bufs = [ctypes.create_string_buffer(max(1, b)) for b in (hkb, hkb, fkb, fkb)]
+    slot = np.zeros(max(1, idx.size), dtype=np.int64)
+    if seed is not None and len(seed) != 32:
+        raise ValueError("seed must be 32 bytes")
+    _check(_lib.pir_hotfull_keygen(full_rows, hot.ctypes.data, hot.size, idx.ctypes.data if idx.size else None,
+                                   idx.size, q_hot, q_full, prf, _buf(seed) if seed is not None else None,
+                                   *[ctypes.cast(b, ctypes.c_void_p) for b in bufs], slot.ctypes.data),
+           "pir_hotfull_keygen")
+    return (bufs[0].raw[:hkb], bufs[1].raw[:hkb], bufs[2].raw[:fkb], bufs[3].raw[:fkb], slot[:idx.size].copy())
+
+
 def pir_key_check(key: bytes):
     n = ctypes.c_uint32()
     party = ctypes.c_uint32()
@@ -254,6 +324,15 @@ PIR_CONTRACT_IMAD = 0
 PIR_CONTRACT_MMA_U8 = 1
 PIR_CONTRACT_SCAN = 2
 PIR_FAULT_WAIT_TIMEOUT = 1
+
+
+def pir_server_eval_pbr(table, bin_rows: int, dkeys, dout, dstatus=None, stream=None):
+    """Partial batch retrieval, server side: dout[b] = bin b's share (device)."""
+    tb = table_of(table)
+    _check(_lib.pir_server_eval_pbr(ctypes.byref(tb), bin_rows, dkeys.data_ptr(), dout.data_ptr(),
+                                    dstatus.data_ptr() if dstatus is not None else None, _stream(stream)),
+           "pir_server_eval_pbr")
+    return dout
 
 
 def pir_expand_materialise(rows: int, dkeys, batch: int, dshares, dstatus=None, stream=None):

@@ -257,6 +257,35 @@ int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t doma
     return pir::eval_device(shard, row_lo, pir_domain_bits(domain_rows), dkeys, batch, dout, dstatus, nullptr, stream);
 }
 
+int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dkeys, uint32_t* dout,
+                        uint32_t* dstatus, void* stream) {
+    using namespace pir;
+    if (!table_ok(t) || !dkeys || !dout || bin_rows < 2) return PIR_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+    if (!vec_ok(t)) return PIR_ERR_UNSUPPORTED;
+    const uint32_t n = pir_domain_bits(bin_rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    const uint64_t nbins = (t->rows + bin_rows - 1) / bin_rows;
+    if (nbins > 0xffffffffull) return PIR_ERR_UNSUPPORTED;
+    pir_plan plan{};
+    int rc = plan_bins(bin_rows, n, t->width, (uint32_t)nbins, &plan);
+    if (rc != PIR_OK) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(dout, 0, nbins * t->width * sizeof(uint32_t), s), "memset shares");
+    EvalRequest req{};
+    req.table = t->data;
+    req.row_lo = 0;
+    req.row_hi = t->rows;
+    req.width = t->width;
+    req.stride = t->stride;
+    req.n = n;
+    req.dkeys = dkeys;
+    req.batch = (uint32_t)nbins;
+    req.dout = dout;
+    req.dstatus = dstatus;
+    return launch_bins(req, bin_rows, plan, stream);
+}
+
 int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, uint32_t* dshares, uint64_t ld,
                            uint32_t* dstatus, void* stream) {
     using namespace pir;

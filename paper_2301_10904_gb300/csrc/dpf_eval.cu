@@ -69,7 +69,7 @@ constexpr int kSplitWords = 2 * kProducers * 4;
 constexpr int kYRegionWords = kYWords > kSplitWords ? kYWords : kSplitWords;
 constexpr int kHdrOff = kYOff + 4 * kYRegionWords;
 constexpr int kMaxGroup = 8;
-constexpr int kHdrBytes = 32 * kMaxGroup;                  // per query: key ptr, out ptr, ok, party, cw_out
+constexpr int kHdrBytes = 48 * kMaxGroup;                  // per query slot: QueryHdr
 constexpr int kItemOff = kHdrOff + kHdrBytes;              // work-item index broadcast (multi-table kernel)
 constexpr int kSmemBytes = kItemOff + 16;
 static_assert(kSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
@@ -105,13 +105,18 @@ struct FusedParams {
     uint32_t* shares;
     uint64_t ld;
     uint32_t shares_vec;  // 1 when shares and ld allow 16-byte stores
+    // bins mode (partial batch retrieval): query q covers rows [q*bin_rows, ...)
+    uint64_t bin_rows;
 };
 
 struct QueryHdr {  // one per query slot of the current item, in shared memory
     const uint8_t* key;
     uint32_t* out;
     uint32_t ok, party, cw_out, prf;
+    const uint32_t* trow;  // bins mode: the slot's first table row
+    uint64_t rows;         // bins mode: rows in the slot's bin
 };
+static_assert(sizeof(QueryHdr) * kMaxGroup <= kHdrBytes, "query slot headers exceed their region");
 
 __device__ __forceinline__ QueryHdr* hdr_slot(int g) { return reinterpret_cast<QueryHdr*>(sm + kHdrOff) + g; }
 
@@ -410,6 +415,55 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
     }
 }
 
+// Bins mode (partial batch retrieval): the G slots are G bins, each with its
+// own rows.  The consumers form G teams of kConsumers/G threads; team g
+// multiplies only slot g's shares, against slot g's rows (bin-relative index
+// r0 + (l << m) + 2*kbase + j), into acc[0].  128-bit loads only.
+template <int G>
+__device__ __forceinline__ void mac_phase_bins(const FusedParams& p, const uint32_t* yb, uint64_t r0, int m, int sd,
+                                               uint32_t kbase, uint32_t kc, uint32_t (&acc)[G][4], uint32_t ct) {
+    constexpr int SQ = kProducers / G;
+    constexpr uint32_t kTeam = kConsumers / G;
+    const uint32_t g = ct / kTeam, t = ct % kTeam;
+    const uint32_t nc = p.width / 4u;
+    const uint32_t nrg = kTeam / nc;
+    const uint32_t c = t % nc, rg = t / nc;
+    const QueryHdr* h = hdr_slot((int)g);
+    if (rg >= nrg || !h->out) return;
+    const uint32_t* trow = h->trow;
+    const uint64_t bin_rows = h->rows;
+    const uint32_t* ys = yb + g * 2 * kPairs * SQ;
+    const uint32_t nrows = (2u * kc) << sd;
+    const uint32_t submask = (1u << sd) - 1u;
+    constexpr int U = 8;
+    for (uint32_t rr0 = rg; rr0 < nrows; rr0 += U * nrg) {
+        uint32_t tv[U][4];
+        uint32_t yi[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t rr = rr0 + u * nrg;
+            const uint32_t j = rr >> sd, l = rr & submask;
+            const uint64_t rel = r0 + ((uint64_t)l << m) + 2ull * kbase + j;
+            ok[u] = rr < nrows && rel < bin_rows;
+            yi[u] = j * SQ + l;
+            if (ok[u]) {
+                load_row<4>(trow + rel * p.stride + (uint64_t)c * 4u, tv[u]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tv[u][i] = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
+            const uint32_t y = ys[yi[u]];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[0][i] += y * tv[u][i];
+        }
+    }
+}
+
 // Writes this thread's last 2*kc leaf shares (rows row_base .. row_base+2kc-1)
 // to the materialised share matrix.
 template <int G>
@@ -437,7 +491,7 @@ __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t
 // with kConsumers consumer threads after the kProducers producers;
 // MAT = true: producers only, leaf shares written to each slot's `out`.
 // Ends with a barrier, so shared memory is free for the next item.
-template <int G, int VEC, bool MAT>
+template <int G, int VEC, bool MAT, bool BINS>
 __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     constexpr int SQ = kProducers / G;
     constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
@@ -529,7 +583,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     // fit there.  (With more queries per item the rows are reused G times and
     // the prefetch only costs issue slots.)
     bool pf = false;
-    if constexpr (G <= 2 && VEC == 4 && !MAT) {
+    if constexpr (G <= 2 && VEC == 4 && !MAT && !BINS) {
         const uint64_t pair_bytes = (uint64_t)nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
         while (kc > 1 && pair_bytes * kc > kPrefetchMaxBytes) kc >>= 1;
         pf = pair_bytes * kc <= kPrefetchMaxBytes;
@@ -605,7 +659,10 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
         for (uint32_t ph = 0; ph < nphases; ++ph) {
             if (pf && ph + 1 < nphases) prefetch_phase(p, r0, m, (uint32_t)nsub, (ph + 1) * kc, kc, ct);
             bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
-            mac_phase<G, VEC>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
+            if constexpr (BINS)
+                mac_phase_bins<G>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
+            else
+                mac_phase<G, VEC>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
             if (ph + 2 < nphases) bar_arrive(kBarFree + (int)(ph & 1u), kFusedThreads);
         }
     }
@@ -617,7 +674,19 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     uint32_t* red = ybuf;
     for (uint32_t i = tid; i < G * W; i += NT) red[i] = 0;
     __syncthreads();
-    if (!producer) {
+    if (!producer && BINS) {
+        // team g holds slot g's partial sums in acc[0]
+        const uint32_t ct = (uint32_t)(tid - kProducers);
+        constexpr uint32_t kTeam = kConsumers / G;
+        const uint32_t g = ct / kTeam, t = ct % kTeam;
+        const uint32_t nc = W / VEC, nrg = kTeam / nc;
+        const uint32_t c = t % nc, rg = t / nc;
+        if (rg < nrg) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i)
+                if (acc[0][i]) atomicAdd(&red[g * W + c * VEC + i], acc[0][i]);
+        }
+    } else if (!producer) {
         const uint32_t ct = (uint32_t)(tid - kProducers);
         const uint32_t nc = W / VEC, nrg = kConsumers / nc;
         const uint32_t c = ct % nc, rg = ct / nc;
@@ -641,7 +710,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
 
 // Persistent grid over items (query group, row range), query groups fastest so
 // that items running at the same time share table rows through L2.
-template <int G, int VEC, bool MAT>
+template <int G, int VEC, bool MAT, bool BINS>
 __device__ __forceinline__ void eval_items(const FusedParams& p) {
     if (!smem_base_ok(p.status)) return;
     build_tables(threadIdx.x);
@@ -652,6 +721,11 @@ __device__ __forceinline__ void eval_items(const FusedParams& p) {
             const uint32_t q = qg * G + threadIdx.x;
             QueryHdr* h = hdr_slot(threadIdx.x);
             const bool valid = q < p.batch;
+            if constexpr (BINS) {  // slot = bin q: rows [q * bin_rows, min(+bin_rows, row_hi))
+                const uint64_t first = (uint64_t)q * p.bin_rows;
+                h->trow = valid ? p.table + first * p.stride : nullptr;
+                h->rows = valid ? (p.row_hi - first < p.bin_rows ? p.row_hi - first : p.bin_rows) : 0;
+            }
             h->key = valid ? p.keys + (uint64_t)q * p.key_bytes : nullptr;
             if constexpr (MAT)
                 h->out = valid ? p.shares + (uint64_t)q * p.ld : nullptr;
@@ -659,18 +733,24 @@ __device__ __forceinline__ void eval_items(const FusedParams& p) {
                 h->out = valid ? p.out + (uint64_t)q * p.width : nullptr;
         }
         __syncthreads();
-        run_item<G, VEC, MAT>(p, r0);
+        run_item<G, VEC, MAT, BINS>(p, r0);
     }
 }
 
 template <int G, int VEC>
 __global__ void __launch_bounds__(kFusedThreads, 1) fused_eval_kernel(const FusedParams p) {
-    eval_items<G, VEC, false>(p);
+    eval_items<G, VEC, false, false>(p);
+}
+
+// Partial batch retrieval: G bins per work item, each slot with its own rows.
+template <int G>
+__global__ void __launch_bounds__(kFusedThreads, 1) bins_eval_kernel(const FusedParams p) {
+    eval_items<G, 4, false, true>(p);
 }
 
 template <int G>
 __global__ void __launch_bounds__(kProducers, 1) expand_materialise_kernel(const FusedParams p) {
-    eval_items<G, 1, true>(p);
+    eval_items<G, 1, true, false>(p);
 }
 
 // Many tables of different sizes and widths in one launch.  Items are
@@ -705,7 +785,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const Mult
             h->out = q != kNoQuery ? mp.out + mp.out_off[q] : nullptr;
         }
         __syncthreads();
-        run_item<kMaxGroup, VEC, false>(p, w.range << tb.range_log2);
+        run_item<kMaxGroup, VEC, false, false>(p, w.range << tb.range_log2);
     }
 }
 
@@ -861,6 +941,56 @@ int launch_multi(const MultiParams& mp, bool vec, void* stream) {
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "multi_eval launch");
+}
+
+// Partial batch retrieval: `batch` bins of bin_rows rows (the last clipped to
+// the table), n = pir_domain_bits(bin_rows).  G bins per item, as many as the
+// consumer teams allow (W/4 column chunks per team of kConsumers/G threads);
+// item row ranges as for a batch of that many queries over one bin.
+int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir_plan* plan) {
+    if (width == 0 || nbins == 0 || n == 0 || width % 4) return PIR_ERR_ARG;
+    uint32_t g = 8;
+    while (g > 1 && (g > nbins || (uint64_t)g * width > (uint64_t)dev::kYRegionWords ||
+                     width / 4 > (uint32_t)dev::kConsumers / g))
+        g >>= 1;
+    if (width / 4 > (uint32_t)dev::kConsumers / g || (uint64_t)g * width > (uint64_t)dev::kYRegionWords)
+        return PIR_ERR_UNSUPPORTED;
+    pir_plan pl{};
+    pl.vec = 4;
+    pl.group = g;
+    const uint32_t nqg = (nbins + g - 1) / g;
+    const int lsq = log_sq(g);
+    int r = std::min((int)n, lsq + dev::kMaxDfsDepth);
+    const int r_min = std::min((int)n, lsq + 1);
+    const int sms = std::max(1, device_sm_count());
+    const uint64_t target = (uint64_t)sms * (nbins >= 8 ? 6 : 1);
+    while (r > r_min && items_for(0, bin_rows, (uint32_t)r, nqg) < target) --r;
+    pl.range_log2 = (uint32_t)r;
+    pl.ctas = (uint32_t)std::min<uint64_t>(items_for(0, bin_rows, (uint32_t)r, nqg), (uint64_t)sms);
+    *plan = pl;
+    return PIR_OK;
+}
+
+int launch_bins(const EvalRequest& req, uint64_t bin_rows, const pir_plan& plan, void* stream) {
+    if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
+    // items: (bin group, range within a bin); every bin spans bin_rows rows of its tree
+    EvalRequest one = req;
+    one.row_lo = 0;
+    one.row_hi = bin_rows;
+    dev::FusedParams p = make_params(one, plan);
+    p.row_hi = req.row_hi;  // the table's rows: clips the last bin
+    p.bin_rows = bin_rows;
+    if (p.nitems == 0) return PIR_OK;
+    const uint32_t ctas = grid_for(p.nitems);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    switch (plan.group) {
+        case 1: e = dev::launch_kernel(dev::bins_eval_kernel<1>, p, ctas, dev::kFusedThreads, s); break;
+        case 2: e = dev::launch_kernel(dev::bins_eval_kernel<2>, p, ctas, dev::kFusedThreads, s); break;
+        case 4: e = dev::launch_kernel(dev::bins_eval_kernel<4>, p, ctas, dev::kFusedThreads, s); break;
+        default: e = dev::launch_kernel(dev::bins_eval_kernel<8>, p, ctas, dev::kFusedThreads, s); break;
+    }
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "bins_eval launch");
 }
 
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {

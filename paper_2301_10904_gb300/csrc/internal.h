@@ -89,6 +89,9 @@ int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t wi
                pir_plan* plan);
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream);
+// partial batch retrieval: req.batch bins of bin_rows rows, req.row_hi = table rows
+int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir_plan* plan);
+int launch_bins(const EvalRequest& req, uint64_t bin_rows, const pir_plan& plan, void* stream);
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream);
 
 // share matrix x table mod 2^32 (contract.cu); out is accumulated into

@@ -7,9 +7,13 @@
 // parties' children equal off the path to alpha and keeps their control bits
 // different on it; a final output word makes the two leaf shares at alpha sum
 // to beta in Z_2^32.
+#include <algorithm>
+#include <atomic>
 #include <cerrno>
 #include <cstdio>
 #include <cstring>
+#include <thread>
+#include <vector>
 
 #include <sys/random.h>
 
@@ -201,6 +205,109 @@ int pir_keygen_prf(uint32_t n, uint64_t alpha, uint32_t beta, uint32_t prf, cons
     std::memcpy(key1 + 16, root1, 16);
     delete[] rnd;
     return PIR_OK;
+}
+
+int pir_keygen_batch(uint32_t n, size_t count, const uint64_t* alphas, const uint32_t* betas, uint32_t prf,
+                     const uint8_t* seed, uint8_t* keys0, uint8_t* keys1, uint32_t threads) {
+    using namespace pir;
+    if (count == 0) return PIR_OK;
+    if (!alphas || !keys0 || !keys1 || n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_ARG;
+    if (prf != PIR_PRF_AES128 && prf != PIR_PRF_CHACHA20) return PIR_ERR_ARG;
+    for (size_t i = 0; i < count; ++i)
+        if ((alphas[i] >> n) != 0) return PIR_ERR_DOMAIN;
+    // one 32-byte seed per key, drawn in key order from the master seed's stream
+    uint8_t master[32];
+    if (seed) {
+        std::memcpy(master, seed, 32);
+    } else if (!os_entropy(master, 32)) {
+        return PIR_ERR_ARG;
+    }
+    std::vector<uint8_t> seeds(32 * count);
+    CtrStream(master).fill(seeds.data(), seeds.size());
+    const size_t kb = key_bytes(n);
+    unsigned nt = threads ? threads : std::max(1u, std::thread::hardware_concurrency());
+    nt = (unsigned)std::min<size_t>(nt, count);
+    std::atomic<size_t> next{0};
+    std::atomic<int> rc{PIR_OK};
+    auto work = [&] {
+        for (size_t i; (i = next.fetch_add(1)) < count;) {
+            const int r = pir_keygen_prf(n, alphas[i], betas ? betas[i] : 1u, prf, seeds.data() + 32 * i,
+                                         keys0 + i * kb, keys1 + i * kb);
+            if (r != PIR_OK) rc.store(r);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    return rc.load();
+}
+
+int pir_pbr_keygen(uint64_t rows, uint64_t bin_rows, const uint64_t* indices, size_t count, uint32_t prf,
+                   const uint8_t* seed, uint8_t* keys0, uint8_t* keys1, uint8_t* kept) {
+    using namespace pir;
+    if (!keys0 || !keys1 || (count && (!indices || !kept)) || bin_rows < 2 || rows == 0) return PIR_ERR_ARG;
+    const uint32_t nb = pir_domain_bits(bin_rows);
+    if (nb == 0) return PIR_ERR_ARG;
+    const uint64_t nbins = (rows + bin_rows - 1) / bin_rows;
+    std::vector<uint64_t> alpha(nbins, 0);
+    std::vector<uint32_t> beta(nbins, 0);  // bins nobody asked for: dummy queries with beta = 0
+    for (size_t i = 0; i < count; ++i) {
+        if (indices[i] >= rows) return PIR_ERR_DOMAIN;
+        const uint64_t b = indices[i] / bin_rows;
+        kept[i] = beta[b] == 0 ? 1 : 0;  // one entry per bin: the first index that falls in it
+        if (kept[i]) {
+            alpha[b] = indices[i] - b * bin_rows;
+            beta[b] = 1;
+        }
+    }
+    return pir_keygen_batch(nb, nbins, alpha.data(), beta.data(), prf, seed, keys0, keys1, 0);
+}
+
+int pir_hotfull_keygen(uint64_t full_rows, const uint64_t* hot_rows, uint64_t hot_count, const uint64_t* indices,
+                       size_t count, uint32_t q_hot, uint32_t q_full, uint32_t prf, const uint8_t* seed,
+                       uint8_t* hot_keys0, uint8_t* hot_keys1, uint8_t* full_keys0, uint8_t* full_keys1,
+                       int64_t* slot) {
+    using namespace pir;
+    if (full_rows < 2 || hot_count < 2 || hot_count > full_rows || !hot_rows || (count && (!indices || !slot)))
+        return PIR_ERR_ARG;
+    if ((q_hot && (!hot_keys0 || !hot_keys1)) || (q_full && (!full_keys0 || !full_keys1))) return PIR_ERR_ARG;
+    for (uint64_t h = 0; h < hot_count; ++h)
+        if (hot_rows[h] >= full_rows || (h && hot_rows[h] <= hot_rows[h - 1])) return PIR_ERR_ARG;
+    // fixed budgets: exactly q_hot queries to the hot table and q_full to the full one
+    std::vector<uint64_t> ha(q_hot, 0), fa(q_full, 0);
+    std::vector<uint32_t> hb(q_hot, 0), fb(q_full, 0);  // beta 0: dummy queries
+    uint32_t nh = 0, nf = 0;
+    for (size_t i = 0; i < count; ++i) {
+        if (indices[i] >= full_rows) return PIR_ERR_DOMAIN;
+        const uint64_t* it = std::lower_bound(hot_rows, hot_rows + hot_count, indices[i]);
+        const bool hot = it != hot_rows + hot_count && *it == indices[i];
+        if (hot && nh < q_hot) {
+            ha[nh] = (uint64_t)(it - hot_rows);
+            hb[nh] = 1;
+            slot[i] = nh++;
+        } else if (nf < q_full) {
+            fa[nf] = indices[i];
+            fb[nf] = 1;
+            slot[i] = (int64_t)q_hot + nf++;
+        } else {
+            slot[i] = -1;  // over both budgets: dropped
+        }
+    }
+    // the hot and the full keys come from two seeds drawn from `seed`'s stream
+    uint8_t masters[64];
+    if (seed) {
+        CtrStream(seed).fill(masters, 64);
+    } else if (!os_entropy(masters, 64)) {
+        return PIR_ERR_ARG;
+    }
+    int rc = q_hot ? pir_keygen_batch(pir_domain_bits(hot_count), q_hot, ha.data(), hb.data(), prf, masters,
+                                      hot_keys0, hot_keys1, 0)
+                   : PIR_OK;
+    if (rc == PIR_OK && q_full)
+        rc = pir_keygen_batch(pir_domain_bits(full_rows), q_full, fa.data(), fb.data(), prf, masters + 32, full_keys0,
+                              full_keys1, 0);
+    return rc;
 }
 
 int pir_key_check(const uint8_t* key, size_t len, uint32_t* n, uint32_t* party) {

@@ -30,6 +30,13 @@ MULTI_TABLE_WIDTHS = [16, 32, 32, 64, 64, 128, 32, 16]
 MULTI_TABLE_QUERIES = 2048
 LARGE_16M = dict(rows=1 << 24, width=32, batch=1024)             # 2 GiB table
 SERVING_TABLES = [(1 << 18, 64), (1 << 20, 32), (1 << 22, 32), (1 << 24, 16)]
+# hot/full split serving: a full table, its 2^18 most popular rows as the hot
+# table, requests of HOTFULL_WANTED rows each (Zipf 1.1 popularity), fixed
+# budgets of hot and full queries per request
+HOTFULL_FULL = (1 << 22, 32)
+HOTFULL_HOT_ROWS = 1 << 18
+HOTFULL_WANTED = 10
+HOTFULL_Q_HOT, HOTFULL_Q_FULL = 10, 3
 
 
 def splitmix64_stream(seed: int, start: int, count: int) -> np.ndarray:
@@ -118,6 +125,28 @@ def zipf_assignment(seed: int, ntables: int, count: int, s: float = 1.1) -> np.n
     p /= p.sum()
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.choice(ntables, size=count, p=p).astype(np.int32)
+
+
+class ZipfRows:
+    """Row popularity of an embedding table: rank k (1-based) is drawn with
+    probability proportional to k^-s, and rank k is row perm[k-1] of a seeded
+    permutation, so popular rows are scattered over the table."""
+
+    def __init__(self, seed: int, rows: int, s: float = 1.1):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.perm = rng.permutation(rows)
+        w = np.arange(1, rows + 1, dtype=np.float64) ** (-s)
+        self.cdf = np.cumsum(w)
+        self.cdf /= self.cdf[-1]
+
+    def top(self, k: int) -> np.ndarray:
+        """The k most popular rows, increasing."""
+        return np.sort(self.perm[:k]).astype(np.uint64)
+
+    def sample(self, seed: int, count: int) -> np.ndarray:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        ranks = np.searchsorted(self.cdf, rng.random(count), side="right")
+        return self.perm[np.minimum(ranks, self.perm.size - 1)].astype(np.uint64)
 
 
 def poisson_arrivals(seed: int, rate_qps: float, count: int) -> np.ndarray:
