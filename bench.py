@@ -229,6 +229,7 @@ def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float =
 # ----------------------------------------------------------------------------- our arm
 
 def kernel_source_digest() -> str:
+    """sha256[:16] of the fused kernels' source (the file every profiled kernel comes from)."""
     src = os.path.join(ROOT, "paper_2301_10904_gb300", "csrc", "dpf_eval.cu")
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
@@ -964,7 +965,7 @@ def run_ours(args):
         "gpu_launches": steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": unit,
                      "frac": round(achieved / peak, 4),
-                     "traffic": profiled_traffic(args.workload) if getattr(W, "prf", 0) == 0 else None,
+                     "traffic": profiled_traffic(args.workload + (":chacha20" if getattr(W, "prf", 0) == 1 else "")),
                      "kernel": W.kernel, "kernel_ms": round(kernel_ms, 4), "work": work, "peak_basis": basis},
         "e2e": {"value": round(W.queries_per_step * world * e2e_steps / (e2e_total / 1e3), 2), "unit": "queries/s",
                 "h2d_bytes_per_step": W.h2d_bytes, "d2h_bytes_per_step": W.d2h_bytes,

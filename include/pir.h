@@ -190,7 +190,12 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
  * bytes, 16-byte aligned.  dout: device, batch x width words, overwritten.
  * dstatus: optional device word; PIR_STATUS_BAD_KEY is OR-ed into it when a
  * key fails validation on the device, and that query's share is 0.
- * Asynchronous on `stream`. */
+ * Strategy: the fused kernel, except for a single query against a table of
+ * 256 MiB or more with 16-byte rows (stride <= 1024), which is expanded into
+ * stream-ordered scratch of rows x 4 bytes from the library's pool and
+ * contracted by the streaming scan (Sec. 3.2.2's level-by-level strategy;
+ * faster there on GB300).  Same result bit for bit.  Asynchronous on
+ * `stream`. */
 int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                            uint32_t* dstatus, void* stream);
 
@@ -358,9 +363,13 @@ void pir_server_destroy(pir_server* server);
 /* Sec. 4 (batch PIR, after [multihot]): key b is a DPF over bin b of the
  * table, rows [b * bin_rows, min((b + 1) * bin_rows, t->rows)), and
  *   dout[b][w] = sum_{j < rows of bin b} Eval(k_b, j) * T[b * bin_rows + j][w]   (mod 2^32)
- * for b < nbins = ceil(t->rows / bin_rows).  One launch: every CTA work item
- * holds up to 8 bins side by side (each with its own rows), so a bin of a
- * few thousand rows still fills the GPU.  dkeys: device, nbins *
+ * for b < nbins = ceil(t->rows / bin_rows).  Strategy: when bin_rows is a
+ * multiple of the streaming scan's chunk (e.g. powers of two >= 256 rows at
+ * 16-64-word rows), every bin's share vector is expanded into stream-ordered
+ * scratch (nbins x bin_rows x 4 bytes from the library's pool) and the table
+ * is streamed once, each chunk of rows multiplying its own bin's shares;
+ * otherwise one fused launch in which every CTA work item holds up to 8 bins
+ * side by side, each with its own rows.  Same result bit for bit.  dkeys: device, nbins *
  * pir_key_bytes(pir_domain_bits(bin_rows)) bytes, 16-byte aligned (as
  * written by pir_pbr_keygen).  dout: device, nbins x width, overwritten.
  * dstatus: as pir_server_eval_device.  Needs bin_rows >= 2, 16-byte aligned

@@ -114,6 +114,46 @@ static bool tuned_plan(uint64_t rows, uint32_t width, size_t batch, bool vec, pi
 
 // Runs the fused evaluation of rows [row_lo, row_lo + shard->rows) of a
 // 2^n-leaf domain for device keys into a zeroed device output.
+// One query against a table of at least kTwoPassMinBytes: expanding its share
+// vector into scratch (the level-by-level strategy, Sec. 3.2.2) and streaming the
+// table once through the scan engine beats the fused kernel, whose product side
+// cannot keep enough loads in flight for a single query (GB300: 136 vs 177 us at
+// 2^20 x 64 words, 1.10 vs 1.29 ms at 2^24 x 32; from two queries on the fused
+// kernel is as fast or faster).  The scratch (rows x 4 bytes) comes from the
+// staging pool.
+constexpr uint64_t kTwoPassMinBytes = 256ull << 20;
+
+static int eval_two_pass(const pir_table* t, uint32_t n, const uint8_t* dkeys, size_t batch, uint32_t* dout,
+                         uint32_t* dstatus, void* stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t ld = (t->rows + 3) & ~3ull;
+    cudaMemPool_t pool = nullptr;
+    int rc = staging_pool(&pool);
+    if (rc != PIR_OK) return rc;
+    pir_plan plan{};
+    rc = plan_fused(t->rows, 0, n, 1, (uint32_t)batch, false, &plan);
+    if (rc != PIR_OK) return rc;
+    uint32_t* S = nullptr;
+    CUDA_TRY(cudaMallocFromPoolAsync((void**)&S, ld * batch * sizeof(uint32_t), pool, s), "alloc share vectors");
+    EvalRequest req{};
+    req.row_lo = 0;
+    req.row_hi = t->rows;
+    req.width = 1;
+    req.stride = 1;
+    req.n = n;
+    req.dkeys = dkeys;
+    req.batch = (uint32_t)batch;
+    req.dstatus = dstatus;
+    rc = launch_materialise(req, plan, S, ld, stream);
+    if (rc == PIR_OK) {
+        cudaError_t e = cudaMemsetAsync(dout, 0, batch * t->width * sizeof(uint32_t), s);
+        rc = e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "memset shares");
+    }
+    if (rc == PIR_OK) rc = launch_scan(S, ld, (uint32_t)batch, t->data, t->stride, t->width, t->rows, dout, stream);
+    cudaFreeAsync(S, s);
+    return rc;
+}
+
 static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
                        uint32_t* dout, uint32_t* dstatus, const pir_plan* plan_in, void* stream) {
     if (!table_ok(shard) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
@@ -121,6 +161,9 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     if (n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_DOMAIN;
     if (row_lo + shard->rows > (1ull << n)) return PIR_ERR_DOMAIN;
     const bool v = vec_ok(shard);
+    if (!plan_in && batch == 1 && row_lo == 0 && (uint64_t)shard->rows * shard->width * 4u >= kTwoPassMinBytes &&
+        v && shard->stride <= 1024)  // the scan engine's layout (its scratch is 16-byte aligned, ld % 4 == 0)
+        return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
     pir_plan plan{};
     if (plan_in) {
         plan = *plan_in;
@@ -267,10 +310,42 @@ int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dk
     if (n == 0) return PIR_ERR_DOMAIN;
     const uint64_t nbins = (t->rows + bin_rows - 1) / bin_rows;
     if (nbins > 0xffffffffull) return PIR_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (scan_bins_supported(t->data, t->stride, t->width, bin_rows)) {
+        // two passes: every bin's share vector into scratch (one word per table row,
+        // nbins x bin_rows words from the staging pool), then one streaming pass over
+        // the table in which each chunk of rows multiplies its own bin's shares
+        // (1.5-2x the fused bins kernel on GB300, whose product side cannot keep
+        // enough loads in flight when no row is shared between queries)
+        cudaMemPool_t pool = nullptr;
+        int rc = staging_pool(&pool);
+        if (rc != PIR_OK) return rc;
+        pir_plan plan{};
+        rc = plan_fused(bin_rows, 0, n, 1, (uint32_t)nbins, false, &plan);
+        if (rc != PIR_OK) return rc;
+        uint32_t* S = nullptr;
+        CUDA_TRY(cudaMallocFromPoolAsync((void**)&S, nbins * bin_rows * sizeof(uint32_t), pool, s), "alloc bin shares");
+        EvalRequest req{};
+        req.row_lo = 0;
+        req.row_hi = bin_rows;
+        req.width = 1;
+        req.stride = 1;
+        req.n = n;
+        req.dkeys = dkeys;
+        req.batch = (uint32_t)nbins;
+        req.dstatus = dstatus;
+        rc = launch_materialise(req, plan, S, bin_rows, stream);
+        if (rc == PIR_OK) {
+            cudaError_t e = cudaMemsetAsync(dout, 0, nbins * t->width * sizeof(uint32_t), s);
+            rc = e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "memset shares");
+        }
+        if (rc == PIR_OK) rc = launch_scan_bins(S, t->data, t->stride, t->width, t->rows, bin_rows, dout, stream);
+        cudaFreeAsync(S, s);
+        return rc;
+    }
     pir_plan plan{};
     int rc = plan_bins(bin_rows, n, t->width, (uint32_t)nbins, &plan);
     if (rc != PIR_OK) return rc;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(dout, 0, nbins * t->width * sizeof(uint32_t), s), "memset shares");
     EvalRequest req{};
     req.table = t->data;

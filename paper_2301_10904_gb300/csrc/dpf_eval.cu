@@ -358,6 +358,32 @@ __device__ __forceinline__ void prefetch_phase(const FusedParams& p, uint64_t r0
     }
 }
 
+// The same for every query slot's own bin (bins mode).
+template <int G>
+__device__ __forceinline__ void prefetch_phase_bins(const FusedParams& p, uint64_t r0, int m, uint32_t nsub,
+                                                    uint32_t kbase, uint32_t kc, uint32_t ct) {
+    for (uint32_t i = ct; i < (uint32_t)G * nsub; i += kConsumers) {
+        const uint32_t g = i / nsub, l = i - g * nsub;
+        const QueryHdr* h = hdr_slot((int)g);
+        if (!h->trow) continue;
+        const uint64_t a = r0 + ((uint64_t)l << m) + 2ull * kbase;
+        uint64_t b = a + 2ull * kc;
+        b = b < h->rows ? b : h->rows;
+        if (a >= b) continue;
+        const uint64_t bytes = ((b - a - 1) * p.stride + p.width) * 4ull;
+        prefetch_l2(h->trow + a * p.stride, (uint32_t)bytes);
+    }
+}
+
+template <int G, bool BINS>
+__device__ __forceinline__ void prefetch_rows(const FusedParams& p, uint64_t r0, int m, uint32_t nsub, uint32_t kbase,
+                                              uint32_t kc, uint32_t ct) {
+    if constexpr (BINS)
+        prefetch_phase_bins<G>(p, r0, m, nsub, kbase, kc, ct);
+    else
+        prefetch_phase(p, r0, m, nsub, kbase, kc, ct);
+}
+
 // Named barriers between producers and consumers: kBarFull + b marks share
 // buffer b as filled, kBarFree + b as consumed (barrier 0 is __syncthreads).
 constexpr int kBarFull = 1, kBarFree = 3;
@@ -583,8 +609,9 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     // fit there.  (With more queries per item the rows are reused G times and
     // the prefetch only costs issue slots.)
     bool pf = false;
-    if constexpr (G <= 2 && VEC == 4 && !MAT && !BINS) {
-        const uint64_t pair_bytes = (uint64_t)nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
+    if constexpr ((G <= 2 || BINS) && VEC == 4 && !MAT) {
+        // bins mode: every slot reads its own rows, so the scan never amortises
+        const uint64_t pair_bytes = (BINS ? (uint64_t)G : 1u) * nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
         while (kc > 1 && pair_bytes * kc > kPrefetchMaxBytes) kc >>= 1;
         pf = pair_bytes * kc <= kPrefetchMaxBytes;
     }
@@ -655,9 +682,9 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     } else if constexpr (!MAT) {
         // ---- consumers: multiply every filled buffer into the accumulators ----
         const uint32_t ct = (uint32_t)(tid - kProducers);
-        if (pf) prefetch_phase(p, r0, m, (uint32_t)nsub, 0, kc, ct);
+        if (pf) prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, 0, kc, ct);
         for (uint32_t ph = 0; ph < nphases; ++ph) {
-            if (pf && ph + 1 < nphases) prefetch_phase(p, r0, m, (uint32_t)nsub, (ph + 1) * kc, kc, ct);
+            if (pf && ph + 1 < nphases) prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, (ph + 1) * kc, kc, ct);
             bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
             if constexpr (BINS)
                 mac_phase_bins<G>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
@@ -836,6 +863,30 @@ static uint64_t items_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t n
     return (last - first + 1) * nqg;
 }
 
+// Rows per work item.  An item costs about n dependent PRF levels of latency
+// (the path walk, the split and the subtree depth, each level a few hundred
+// cycles that the SM cannot fill) plus its G x 2^r tree nodes of throughput
+// work; a CTA runs its items one after another.  Pick r minimising
+//   ceil(items / CTAs) x (n x kLevelNodes + G x 2^r),
+// kLevelNodes being one level's latency in units of one node's work at the
+// SM's full rate (~1.4 us against ~4.3 ns, measured on GB300).
+constexpr uint64_t kLevelNodes = 320;
+static int pick_range_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t g, uint32_t nqg, int r_min, int r_max,
+                           int sms) {
+    int best = r_max;
+    double best_cost = -1.0;
+    for (int r = r_max; r >= r_min; --r) {
+        const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
+        const double rounds = (double)((items + (uint64_t)sms - 1) / (uint64_t)sms);
+        const double cost = rounds * ((double)n * (double)kLevelNodes + (double)g * (double)(1ull << r));
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = r;
+        }
+    }
+    return best;
+}
+
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     if (plan.group != 1 && plan.group != 2 && plan.group != 4 && plan.group != 8) return PIR_ERR_UNSUPPORTED;
     if (plan.vec != 1 && plan.vec != 4) return PIR_ERR_UNSUPPORTED;
@@ -861,20 +912,10 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     pl.group = g;
     const uint32_t nqg = (batch + g - 1) / g;
     const int lsq = log_sq(g);
-    int r = std::min((int)n, lsq + dev::kMaxDfsDepth);
     const int sms = std::max(1, device_sm_count());
-    const int r_min = std::min((int)n, lsq + 1);
-    if (batch >= 8) {
-        // batches: shrink the items until there are about six per SM (balance of the
-        // last round)
-        const uint64_t target = (uint64_t)sms * 6;
-        while (r > r_min && items_for(row_lo, rows, (uint32_t)r, nqg) < target) --r;
-    } else {
-        // a few queries: latency.  Every item walks n dependent levels (path, split,
-        // subtree), so give each CTA at most one item: the most items not above the
-        // SM count
-        while (r > r_min && items_for(row_lo, rows, (uint32_t)(r - 1), nqg) <= (uint64_t)sms) --r;
-    }
+    // every producer gets a subtree (r >= log2(512/G) + 1), subtrees at most kMaxDfsDepth deep
+    const int r = pick_range_log2(row_lo, rows, n, g, nqg, std::min((int)n, lsq + 1),
+                                  std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
     pl.range_log2 = (uint32_t)r;
     const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
     pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
@@ -960,11 +1001,9 @@ int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir
     pl.group = g;
     const uint32_t nqg = (nbins + g - 1) / g;
     const int lsq = log_sq(g);
-    int r = std::min((int)n, lsq + dev::kMaxDfsDepth);
-    const int r_min = std::min((int)n, lsq + 1);
     const int sms = std::max(1, device_sm_count());
-    const uint64_t target = (uint64_t)sms * (nbins >= 8 ? 6 : 1);
-    while (r > r_min && items_for(0, bin_rows, (uint32_t)r, nqg) < target) --r;
+    const int r = pick_range_log2(0, bin_rows, n, g, nqg, std::min((int)n, lsq + 1),
+                                  std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
     pl.range_log2 = (uint32_t)r;
     pl.ctas = (uint32_t)std::min<uint64_t>(items_for(0, bin_rows, (uint32_t)r, nqg), (uint64_t)sms);
     *plan = pl;

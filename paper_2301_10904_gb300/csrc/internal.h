@@ -102,6 +102,12 @@ int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const u
 bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width);
 int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                 uint32_t width, uint64_t rows, uint32_t* out, void* stream);
+// the diagonal form (partial batch retrieval): shares[k] belongs to row k and to
+// query k / bin_rows; out[b] = sum over bin b's rows (bin_rows a multiple of the
+// engine's chunk, which scan_bins_supported checks)
+bool scan_bins_supported(const uint32_t* table, uint64_t stride, uint32_t width, uint64_t bin_rows);
+int launch_scan_bins(const uint32_t* shares, const uint32_t* table, uint64_t stride, uint32_t width, uint64_t rows,
+                     uint64_t bin_rows, uint32_t* out, void* stream);
 // library-wide device fault bits (PIR_FAULT_*), read on the current device
 int device_faults(uint32_t* flags, bool clear);
 

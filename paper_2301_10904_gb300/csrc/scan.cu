@@ -10,8 +10,9 @@
 // share words of every query, into a ring of kScanStages shared-memory stages
 // (cp.async.bulk, completion counted in bytes on one mbarrier per stage);
 // 256 threads multiply each chunk into register accumulators while the next
-// stages are in flight.  Consumer (c, rg) owns words 4c..4c+3 for rows rg,
-// rg + nrg, ... of a chunk.  Partial sums meet in shared memory, then one u32
+// stages are in flight.  Consumer (c, rg) owns words 4c..4c+3 of rows
+// 4rg..4rg+3 of a chunk, so that it reads four shares of a query with one
+// 128-bit load.  Partial sums meet in shared memory, then one u32
 // atomicAdd per (query, word) per CTA; addition mod 2^32 is associative, so
 // the result is bit-exact in any order.
 #include <cuda_runtime.h>
@@ -47,6 +48,10 @@ struct ScanParams {
     uint32_t B, W;
     uint32_t R;            // rows per chunk, multiple of 4
     uint32_t stage_bytes;  // R * stride * 4 (table slot) + 8 * R * 4 (share slots)
+    // diagonal form (partial batch retrieval): S is one share per table row, row k
+    // belonging to query k / bin_rows; each CTA takes chunks_per_cta consecutive chunks
+    uint64_t bin_rows;
+    uint64_t chunks_per_cta;
 };
 
 extern __shared__ __align__(128) char scan_sm[];
@@ -98,25 +103,56 @@ __device__ __forceinline__ void scan_issue(const ScanParams& p, uint32_t s, uint
             bulk_g2s(dst + p.R * (uint32_t)p.stride * 4u + b * p.R * 4u, p.S + b * p.ld + k0, sbytes, bar);
 }
 
+// Partial sums of every consumer for `rows` queries, met in shared memory
+// (red, rows x W words), then one u32 atomicAdd per (query, word) into out.
+// Call with every thread of the CTA.
 template <int BQ>
+__device__ __forceinline__ void scan_flush(const ScanParams& p, uint32_t (&acc)[BQ][4], uint32_t* red, uint32_t* out,
+                                           uint32_t cc, bool active) {
+    const uint32_t tid = threadIdx.x;
+    __syncthreads();  // red is free (a previous flush has finished reading it)
+    for (uint32_t i = tid; i < BQ * p.W; i += kScanThreads) red[i] = 0;
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int b = 0; b < BQ; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (acc[b][e]) atomicAdd(&red[b * p.W + 4u * cc + e], acc[b][e]);
+                acc[b][e] = 0;
+            }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < BQ * p.W; i += kScanThreads)
+        if (red[i]) atomicAdd(out + i, red[i]);
+}
+
+template <int BQ, bool DIAG>  // BQ: queries of this pass, exactly; DIAG: one bin's query per chunk (BQ = 1)
 __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanParams p) {
+    static_assert(!DIAG || BQ == 1, "the diagonal form has one query per chunk");
     const uint32_t tid = threadIdx.x;
     uint32_t* verdict = reinterpret_cast<uint32_t*>(scan_sm + 64);
     const uint32_t bar0 = smem_addr(scan_sm);
+    uint32_t* red = reinterpret_cast<uint32_t*>(scan_sm + kScanHeader + kScanStages * p.stage_bytes);
     if (tid == 0) {
         for (int s = 0; s < kScanStages; ++s) mbar_init(bar0 + 8u * s, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const uint64_t G = gridDim.x;
+    // this CTA's chunks, c_first + j * c_step for c < c_end: dealt round-robin, or
+    // (diagonal form) as one contiguous run, so that a bin's chunks stay together
+    const uint64_t c_first = DIAG ? blockIdx.x * p.chunks_per_cta : blockIdx.x;
+    const uint64_t c_step = DIAG ? 1 : gridDim.x;
+    const uint64_t c_end = DIAG ? min(c_first + p.chunks_per_cta, p.nchunks) : p.nchunks;
     if (tid == 0)
         for (uint32_t s = 0; s < (uint32_t)kScanStages; ++s) {
-            const uint64_t c = blockIdx.x + s * G;
-            if (c < p.nchunks) scan_issue(p, s, c);
+            const uint64_t c = c_first + s * c_step;
+            if (c < c_end) scan_issue(p, s, c);
         }
 
+    // consumer (cc, rg): words 4cc..4cc+3 of rows 4rg..4rg+3 of every chunk (R <= 4 nrg)
     const uint32_t nc = p.W / 4, nrg = kScanThreads / nc;
-    const uint32_t cc = tid % nc, rg = tid / nc;
+    const uint32_t cc = tid % nc, rg = tid / nc, i0 = 4u * rg;
     uint32_t acc[BQ][4];
 #pragma unroll
     for (int b = 0; b < BQ; ++b)
@@ -124,8 +160,8 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
         for (int e = 0; e < 4; ++e) acc[b][e] = 0;
 
     bool failed = false;
-    uint64_t j = 0;
-    for (uint64_t c = blockIdx.x; c < p.nchunks; c += G, ++j) {
+    uint64_t j = 0, cur_bin = ~0ull;
+    for (uint64_t c = c_first; c < c_end; c += c_step, ++j) {
         const uint32_t s = (uint32_t)(j % kScanStages), parity = (uint32_t)((j / kScanStages) & 1u);
         if (tid == 0) *verdict = mbar_wait(bar0 + 8u * s, parity) ? 1u : 0u;
         __syncthreads();
@@ -135,16 +171,37 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
         }
         mbar_try_wait(bar0 + 8u * s, parity);  // completed: gives this thread the copies' data
         const uint64_t k0 = c * p.R;
+        if constexpr (DIAG) {
+            const uint64_t bin = k0 / p.bin_rows;  // chunks do not straddle bins
+            if (bin != cur_bin) {
+                if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg);
+                cur_bin = bin;
+            }
+        }
         const uint32_t nr = (uint32_t)(p.K - k0 < p.R ? p.K - k0 : p.R), nr4 = nr & ~3u;
         const char* stage = scan_sm + kScanHeader + s * p.stage_bytes;
         const uint32_t* sS = reinterpret_cast<const uint32_t*>(stage + p.R * (uint32_t)p.stride * 4u);
-        if (rg < nrg) {
-            for (uint32_t i = rg; i < nr; i += nrg) {
+        if (rg < nrg && i0 + 4u <= nr4) {
+            // four whole rows: 128-bit loads of the table words and of each query's four shares
+            uint4 t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                t[u] = *reinterpret_cast<const uint4*>(stage + ((uint64_t)(i0 + u) * p.stride + 4u * cc) * 4u);
+#pragma unroll
+            for (int b = 0; b < BQ; ++b) {
+                const uint4 y = *reinterpret_cast<const uint4*>(sS + b * p.R + i0);
+                acc[b][0] += y.x * t[0].x + y.y * t[1].x + y.z * t[2].x + y.w * t[3].x;
+                acc[b][1] += y.x * t[0].y + y.y * t[1].y + y.z * t[2].y + y.w * t[3].y;
+                acc[b][2] += y.x * t[0].z + y.y * t[1].z + y.z * t[2].z + y.w * t[3].z;
+                acc[b][3] += y.x * t[0].w + y.y * t[1].w + y.z * t[2].w + y.w * t[3].w;
+            }
+        } else if (rg < nrg && i0 < nr) {
+            // the ragged end of the last chunk: shares past nr & ~3 were not copied
+            for (uint32_t i = i0; i < i0 + 4u && i < nr; ++i) {
                 const uint4 t = *reinterpret_cast<const uint4*>(stage + ((uint64_t)i * p.stride + 4u * cc) * 4u);
 #pragma unroll
                 for (int b = 0; b < BQ; ++b) {
-                    uint32_t y = 0;
-                    if ((uint32_t)b < p.B) y = i < nr4 ? sS[b * p.R + i] : __ldg(p.S + b * p.ld + k0 + i);
+                    const uint32_t y = i < nr4 ? sS[b * p.R + i] : __ldg(p.S + b * p.ld + k0 + i);
                     acc[b][0] += y * t.x;
                     acc[b][1] += y * t.y;
                     acc[b][2] += y * t.z;
@@ -153,9 +210,9 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
             }
         }
         __syncthreads();  // stage s is consumed
-        if (tid == 0 && c + kScanStages * G < p.nchunks) {
+        if (tid == 0 && c + kScanStages * c_step < c_end) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            scan_issue(p, s, c + kScanStages * G);
+            scan_issue(p, s, c + kScanStages * c_step);
         }
     }
     if (failed) {
@@ -164,28 +221,18 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
         if (tid == 0) {
             atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
             for (uint64_t jj = j; jj < j + kScanStages; ++jj) {
-                const uint64_t c = blockIdx.x + jj * G;
-                if (c >= p.nchunks) break;
+                const uint64_t c = c_first + jj * c_step;
+                if (c >= c_end) break;
                 mbar_wait(bar0 + 8u * (uint32_t)(jj % kScanStages), (uint32_t)((jj / kScanStages) & 1u));
             }
         }
         return;
     }
-
-    // ---- partial sums of all consumers, then one atomic per (query, word) ----
-    uint32_t* red = reinterpret_cast<uint32_t*>(scan_sm + kScanHeader);
-    for (uint32_t i = tid; i < p.B * p.W; i += kScanThreads) red[i] = 0;
-    __syncthreads();
-    if (rg < nrg) {
-#pragma unroll
-        for (int b = 0; b < BQ; ++b)
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if ((uint32_t)b < p.B && acc[b][e]) atomicAdd(&red[b * p.W + 4u * cc + e], acc[b][e]);
+    if (DIAG) {
+        if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg);
+    } else {
+        scan_flush<BQ>(p, acc, red, p.out, cc, rg < nrg);
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < p.B * p.W; i += kScanThreads)
-        if (red[i]) atomicAdd(p.out + i, red[i]);
 }
 
 }  // namespace dev
@@ -196,43 +243,83 @@ bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, 
            stride <= dev::kScanMaxWidth;
 }
 
-int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
-                uint32_t width, uint64_t rows, uint32_t* out, void* stream) {
-    using namespace dev;
-    if (!scan_supported(shares, ld, table, stride, width)) return PIR_ERR_UNSUPPORTED;
-    uint32_t R = (uint32_t)(kScanTableStageBytes / (stride * 4u)) & ~3u;
-    R = std::min(kScanMaxRows, std::max(4u, R));
-    ScanParams p{};
+static uint32_t scan_rows_per_chunk(uint64_t stride, uint32_t width) {
+    uint32_t R = (uint32_t)(dev::kScanTableStageBytes / (stride * 4u)) & ~3u;
+    R = std::min(dev::kScanMaxRows, std::max(4u, R));
+    return std::min(R, 4u * (uint32_t)(dev::kScanThreads / (width / 4u)));  // four rows per consumer thread
+}
+
+static dev::ScanParams scan_params(uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width,
+                                   uint64_t rows) {
+    dev::ScanParams p{};
     p.ld = ld;
     p.T = table;
     p.stride = stride;
     p.K = rows;
-    p.nchunks = (rows + R - 1) / R;
     p.W = width;
-    p.R = R;
-    p.stage_bytes = R * (uint32_t)stride * 4u + 8u * R * 4u;
-    const size_t smem = kScanHeader + (size_t)kScanStages * p.stage_bytes;
+    p.R = scan_rows_per_chunk(stride, width);
+    p.nchunks = (rows + p.R - 1) / p.R;
+    p.stage_bytes = p.R * (uint32_t)stride * 4u + 8u * p.R * 4u;
+    return p;
+}
+
+// Sets the kernel's shared memory (stages + the reduction area for B queries)
+// and launches it on as many CTAs as fit (at most one per chunk); `ctas` gets
+// the grid size before the launch through `fix` (the diagonal form needs it).
+template <typename Fix>
+static int launch_scan_kernel(void (*kern)(dev::ScanParams), dev::ScanParams p, uint32_t B, cudaStream_t s, Fix fix) {
+    using namespace dev;
+    const size_t smem = kScanHeader + (size_t)kScanStages * p.stage_bytes + (((size_t)B * p.W * 4u + 15u) & ~15ull);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanThreads, smem);
+    if (e != cudaSuccess) return cuda_fail((int)e, "scan setup");
     const int sms = std::max(1, device_sm_count());
+    const uint64_t ctas = std::min<uint64_t>(p.nchunks, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
+    fix(p, ctas);
+    kern<<<(uint32_t)ctas, kScanThreads, smem, s>>>(p);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "scan launch");
+}
+
+int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                uint32_t width, uint64_t rows, uint32_t* out, void* stream) {
+    using namespace dev;
+    if (!scan_supported(shares, ld, table, stride, width)) return PIR_ERR_UNSUPPORTED;
+    ScanParams p = scan_params(ld, table, stride, width, rows);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void (*const kerns[8])(ScanParams) = {contract_scan_kernel<1, false>, contract_scan_kernel<2, false>,
+                                          contract_scan_kernel<3, false>, contract_scan_kernel<4, false>,
+                                          contract_scan_kernel<5, false>, contract_scan_kernel<6, false>,
+                                          contract_scan_kernel<7, false>, contract_scan_kernel<8, false>};
     // eight queries per pass; each pass streams the whole table once
     for (uint32_t b0 = 0; b0 < batch; b0 += 8) {
         p.B = std::min(8u, batch - b0);
         p.S = shares + (uint64_t)b0 * ld;
         p.out = out + (uint64_t)b0 * width;
-        void (*kern)(ScanParams) = p.B > 4 ? contract_scan_kernel<8>
-                                   : p.B > 2 ? contract_scan_kernel<4>
-                                   : p.B > 1 ? contract_scan_kernel<2>
-                                             : contract_scan_kernel<1>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanThreads, smem);
-        if (e != cudaSuccess) return cuda_fail((int)e, "scan setup");
-        const uint64_t ctas = std::min<uint64_t>(p.nchunks, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
-        kern<<<(uint32_t)ctas, kScanThreads, smem, s>>>(p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail((int)e, "scan launch");
+        const int rc = launch_scan_kernel(kerns[p.B - 1], p, p.B, s, [](ScanParams&, uint64_t) {});
+        if (rc != PIR_OK) return rc;
     }
     return PIR_OK;
+}
+
+bool scan_bins_supported(const uint32_t* table, uint64_t stride, uint32_t width, uint64_t bin_rows) {
+    return (reinterpret_cast<uintptr_t>(table) & 15u) == 0 && stride % 4 == 0 && width % 4 == 0 &&
+           stride <= dev::kScanMaxWidth && bin_rows % scan_rows_per_chunk(stride, width) == 0;
+}
+
+int launch_scan_bins(const uint32_t* shares, const uint32_t* table, uint64_t stride, uint32_t width, uint64_t rows,
+                     uint64_t bin_rows, uint32_t* out, void* stream) {
+    using namespace dev;
+    if ((reinterpret_cast<uintptr_t>(shares) & 15u) != 0 || !scan_bins_supported(table, stride, width, bin_rows))
+        return PIR_ERR_UNSUPPORTED;
+    ScanParams p = scan_params(0, table, stride, width, rows);
+    p.B = 1;
+    p.S = shares;
+    p.out = out;
+    p.bin_rows = bin_rows;
+    return launch_scan_kernel(contract_scan_kernel<1, true>, p, 1, reinterpret_cast<cudaStream_t>(stream),
+                              [](ScanParams& q, uint64_t ctas) { q.chunks_per_cta = (q.nchunks + ctas - 1) / ctas; });
 }
 
 int device_faults(uint32_t* flags, bool clear) {

@@ -91,3 +91,36 @@ def test_batched_2p20x64_b256(env):
 
 def test_large_2p24x32_b1024(env):
     _check_config(env, 1 << 24, 32, 1024, 404, [1023])
+
+
+def test_single_query_on_a_large_table_two_pass_strategy(env):
+    """One query on the 2^20 x 64-word table (256 MiB): the library expands the
+    share vector into scratch and streams the table through the scan engine.
+    Both parties' shares equal the fused kernel's (explicit plan) word for
+    word, one equals the oracle's, the pair reconstructs T[alpha], and a bad
+    key gives a zero share and the status bit."""
+    torch, pir, orc = env
+    rows, W = 1 << 20, 64
+    T = wl.table_u32(20, rows, W)
+    table = torch.from_numpy(T.view(np.int32)).cuda()
+    n = pir.pir_domain_bits(rows)
+    alpha = 777_777
+    ks0, ks1 = _keys(orc, n, [alpha], 31)
+    got = [_eval(torch, pir, table, ks, W)[0] for ks in (ks0, ks1)]
+    plan = pir.pir_plan_for(rows, W, 1)
+    for ks, g in zip((ks0, ks1), got):
+        dk = torch.frombuffer(bytearray(ks[0]), dtype=torch.uint8).cuda()
+        fused = torch.empty((1, W), dtype=torch.int32, device="cuda")
+        pir.pir_server_eval_device_plan(table, dk, 1, fused, plan)
+        torch.cuda.synchronize()
+        assert np.array_equal(fused.cpu().numpy().view(np.uint32)[0], g)
+    assert np.array_equal(got[0], orc.answer(ks0[0], T))
+    rec = ((got[0].astype(np.uint64) + got[1]) & 0xFFFFFFFF).astype(np.uint32)
+    assert np.array_equal(rec, T[alpha])
+    bad = bytearray(ks0[0])
+    bad[5] = 3  # wrong n
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.full((1, W), 9, dtype=torch.int32, device="cuda")
+    pir.pir_server_eval_device(table, torch.frombuffer(bad, dtype=torch.uint8).cuda(), 1, out, status)
+    torch.cuda.synchronize()
+    assert not out.any() and int(status.item()) & pir.PIR_STATUS_BAD_KEY
