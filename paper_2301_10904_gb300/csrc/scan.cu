@@ -8,9 +8,11 @@
 //
 // The copy engine streams chunks of R consecutive table rows, and the same R
 // share words of every query, into a ring of kScanStages shared-memory stages
-// (cp.async.bulk, completion counted in bytes on one mbarrier per stage);
-// 256 threads multiply each chunk into register accumulators while the next
-// stages are in flight.  Consumer (c, rg) owns words 4c..4c+3 of rows
+// (cp.async.bulk, completion counted in bytes on a "full" mbarrier per stage).
+// One warp issues the copies; 8 consumer warps multiply each chunk into
+// register accumulators while the next stages are in flight, and release a
+// stage by arriving on its "empty" mbarrier, which the issuing warp waits on
+// before refilling it: no CTA-wide barrier per chunk.  Every wait is bounded.  Consumer (c, rg) owns words 4c..4c+3 of rows
 // 4rg..4rg+3 of a chunk, so that it reads four shares of a query with one
 // 128-bit load.  Partial sums meet in shared memory, then one u32
 // atomicAdd per (query, word) per CTA; addition mod 2^32 is associative, so
@@ -25,12 +27,15 @@
 namespace pir {
 namespace dev {
 
-constexpr int kScanThreads = 256;
+constexpr int kScanConsumers = 256;                 // threads that multiply (8 warps)
+constexpr int kScanConsumerWarps = kScanConsumers / 32;
+constexpr int kScanThreads = kScanConsumers + 32;    // + one warp that issues the copies
 constexpr int kScanStages = 4;
 constexpr uint32_t kScanTableStageBytes = 16384;  // table bytes per stage (target)
 constexpr uint32_t kScanMaxRows = 512;            // rows per chunk cap (bounds the share slots)
 constexpr uint32_t kScanMaxWidth = 1024;          // words per row (R >= 4 keeps stages <= 16 KiB)
-constexpr uint32_t kScanHeader = 128;             // mbarriers + the wait verdict
+constexpr uint32_t kScanHeader = 128;             // full mbarriers [0,32), empty [32,64), abort flag at 64
+constexpr int kScanConsumerBar = 1;               // named barrier of the consumer warps
 constexpr uint32_t kScanSpinLimit = 1u << 22;     // bounded waits (each try_wait may also suspend)
 
 // Set (bitwise) when a wait in one of the library's kernels gave up; read and
@@ -79,6 +84,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kScanConsumerBar), "n"(kScanConsumers) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
@@ -103,16 +114,16 @@ __device__ __forceinline__ void scan_issue(const ScanParams& p, uint32_t s, uint
             bulk_g2s(dst + p.R * (uint32_t)p.stride * 4u + b * p.R * 4u, p.S + b * p.ld + k0, sbytes, bar);
 }
 
-// Partial sums of every consumer for `rows` queries, met in shared memory
-// (red, rows x W words), then one u32 atomicAdd per (query, word) into out.
-// Call with every thread of the CTA.
+// Partial sums of every consumer for BQ queries, met in shared memory (red,
+// BQ x W words), then one u32 atomicAdd per (query, word) into out.  Called
+// by every consumer thread (the issuing warp does not take part).
 template <int BQ>
 __device__ __forceinline__ void scan_flush(const ScanParams& p, uint32_t (&acc)[BQ][4], uint32_t* red, uint32_t* out,
                                            uint32_t cc, bool active) {
     const uint32_t tid = threadIdx.x;
-    __syncthreads();  // red is free (a previous flush has finished reading it)
-    for (uint32_t i = tid; i < BQ * p.W; i += kScanThreads) red[i] = 0;
-    __syncthreads();
+    consumers_sync();  // red is free (a previous flush has finished reading it)
+    for (uint32_t i = tid; i < BQ * p.W; i += kScanConsumers) red[i] = 0;
+    consumers_sync();
     if (active) {
 #pragma unroll
         for (int b = 0; b < BQ; ++b)
@@ -122,36 +133,59 @@ __device__ __forceinline__ void scan_flush(const ScanParams& p, uint32_t (&acc)[
                 acc[b][e] = 0;
             }
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < BQ * p.W; i += kScanThreads)
+    consumers_sync();
+    for (uint32_t i = tid; i < BQ * p.W; i += kScanConsumers)
         if (red[i]) atomicAdd(out + i, red[i]);
 }
 
 template <int BQ, bool DIAG>  // BQ: queries of this pass, exactly; DIAG: one bin's query per chunk (BQ = 1)
-__global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanParams p) {
+__global__ void __launch_bounds__(kScanThreads, 3) contract_scan_kernel(const ScanParams p) {
     static_assert(!DIAG || BQ == 1, "the diagonal form has one query per chunk");
-    const uint32_t tid = threadIdx.x;
-    uint32_t* verdict = reinterpret_cast<uint32_t*>(scan_sm + 64);
-    const uint32_t bar0 = smem_addr(scan_sm);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t full0 = smem_addr(scan_sm), empty0 = full0 + 32u;
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(scan_sm + 64);
     uint32_t* red = reinterpret_cast<uint32_t*>(scan_sm + kScanHeader + kScanStages * p.stage_bytes);
     if (tid == 0) {
-        for (int s = 0; s < kScanStages; ++s) mbar_init(bar0 + 8u * s, 1);
+        for (int s = 0; s < kScanStages; ++s) {
+            mbar_init(full0 + 8u * s, 1);                     // the issuing thread's arrival + the copies' bytes
+            mbar_init(empty0 + 8u * s, kScanConsumerWarps);   // one arrival per consumer warp
+        }
+        *abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
+    __syncthreads();  // the only CTA-wide barrier
     // this CTA's chunks, c_first + j * c_step for c < c_end: dealt round-robin, or
     // (diagonal form) as one contiguous run, so that a bin's chunks stay together
     const uint64_t c_first = DIAG ? blockIdx.x * p.chunks_per_cta : blockIdx.x;
     const uint64_t c_step = DIAG ? 1 : gridDim.x;
     const uint64_t c_end = DIAG ? min(c_first + p.chunks_per_cta, p.nchunks) : p.nchunks;
-    if (tid == 0)
-        for (uint32_t s = 0; s < (uint32_t)kScanStages; ++s) {
-            const uint64_t c = c_first + s * c_step;
-            if (c < c_end) scan_issue(p, s, c);
-        }
 
-    // consumer (cc, rg): words 4cc..4cc+3 of rows 4rg..4rg+3 of every chunk (R <= 4 nrg)
-    const uint32_t nc = p.W / 4, nrg = kScanThreads / nc;
+    if (warp == kScanConsumerWarps) {
+        // ---- the issuing warp: refill a stage once every consumer warp released it ----
+        if (lane == 0) {
+            uint64_t j = 0;
+            for (uint64_t c = c_first; c < c_end; c += c_step, ++j) {
+                const uint32_t s = (uint32_t)(j % kScanStages);
+                if (j >= (uint64_t)kScanStages &&
+                    !mbar_wait(empty0 + 8u * s, (uint32_t)((j / kScanStages - 1) & 1u))) {
+                    atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
+                    *abort_flag = 1u;
+                    break;  // stop issuing; the consumers' bounded waits run out
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // consumers' reads before the refill
+                scan_issue(p, s, c);
+            }
+            // the copies of the last stages issued are this thread's: see them land (bounded)
+            // before it leaves
+            const uint64_t first = j > (uint64_t)kScanStages ? j - kScanStages : 0;
+            for (uint64_t jj = first; jj < j; ++jj)
+                mbar_wait(full0 + 8u * (uint32_t)(jj % kScanStages), (uint32_t)((jj / kScanStages) & 1u));
+        }
+        return;
+    }
+
+    // ---- consumer (cc, rg): words 4cc..4cc+3 of rows 4rg..4rg+3 of every chunk (R <= 4 nrg) ----
+    const uint32_t nc = p.W / 4, nrg = kScanConsumers / nc;
     const uint32_t cc = tid % nc, rg = tid / nc, i0 = 4u * rg;
     uint32_t acc[BQ][4];
 #pragma unroll
@@ -159,29 +193,26 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[b][e] = 0;
 
-    bool failed = false;
     uint64_t j = 0, cur_bin = ~0ull;
     for (uint64_t c = c_first; c < c_end; c += c_step, ++j) {
         const uint32_t s = (uint32_t)(j % kScanStages), parity = (uint32_t)((j / kScanStages) & 1u);
-        if (tid == 0) *verdict = mbar_wait(bar0 + 8u * s, parity) ? 1u : 0u;
-        __syncthreads();
-        if (*verdict == 0u) {
-            failed = true;
-            break;
+        if (!mbar_wait(full0 + 8u * s, parity)) {
+            if (lane == 0) atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
+            *abort_flag = 1u;
         }
-        mbar_try_wait(bar0 + 8u * s, parity);  // completed: gives this thread the copies' data
+        const bool live = *abort_flag == 0u;  // after a failed wait the stages hold nothing trustworthy
         const uint64_t k0 = c * p.R;
         if constexpr (DIAG) {
             const uint64_t bin = k0 / p.bin_rows;  // chunks do not straddle bins
             if (bin != cur_bin) {
-                if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg);
+                if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg && live);
                 cur_bin = bin;
             }
         }
         const uint32_t nr = (uint32_t)(p.K - k0 < p.R ? p.K - k0 : p.R), nr4 = nr & ~3u;
         const char* stage = scan_sm + kScanHeader + s * p.stage_bytes;
         const uint32_t* sS = reinterpret_cast<const uint32_t*>(stage + p.R * (uint32_t)p.stride * 4u);
-        if (rg < nrg && i0 + 4u <= nr4) {
+        if (live && rg < nrg && i0 + 4u <= nr4) {
             // four whole rows: 128-bit loads of the table words and of each query's four shares
             uint4 t[4];
 #pragma unroll
@@ -195,7 +226,7 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
                 acc[b][2] += y.x * t[0].z + y.y * t[1].z + y.z * t[2].z + y.w * t[3].z;
                 acc[b][3] += y.x * t[0].w + y.y * t[1].w + y.z * t[2].w + y.w * t[3].w;
             }
-        } else if (rg < nrg && i0 < nr) {
+        } else if (live && rg < nrg && i0 < nr) {
             // the ragged end of the last chunk: shares past nr & ~3 were not copied
             for (uint32_t i = i0; i < i0 + 4u && i < nr; ++i) {
                 const uint4 t = *reinterpret_cast<const uint4*>(stage + ((uint64_t)i * p.stride + 4u * cc) * 4u);
@@ -209,29 +240,14 @@ __global__ void __launch_bounds__(kScanThreads) contract_scan_kernel(const ScanP
                 }
             }
         }
-        __syncthreads();  // stage s is consumed
-        if (tid == 0 && c + kScanStages * c_step < c_end) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            scan_issue(p, s, c + kScanStages * c_step);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8u * s);  // this warp is done with stage s
     }
-    if (failed) {
-        // a copy never completed: record it, wait (bounded) for the copies this
-        // CTA still has in flight, and leave without touching out
-        if (tid == 0) {
-            atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
-            for (uint64_t jj = j; jj < j + kScanStages; ++jj) {
-                const uint64_t c = c_first + jj * c_step;
-                if (c >= c_end) break;
-                mbar_wait(bar0 + 8u * (uint32_t)(jj % kScanStages), (uint32_t)((jj / kScanStages) & 1u));
-            }
-        }
-        return;
-    }
+    const bool live = *abort_flag == 0u;
     if (DIAG) {
-        if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg);
+        if (cur_bin != ~0ull) scan_flush<BQ>(p, acc, red, p.out + cur_bin * p.W, cc, rg < nrg && live);
     } else {
-        scan_flush<BQ>(p, acc, red, p.out, cc, rg < nrg);
+        scan_flush<BQ>(p, acc, red, p.out, cc, rg < nrg && live);
     }
 }
 
@@ -246,7 +262,7 @@ bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, 
 static uint32_t scan_rows_per_chunk(uint64_t stride, uint32_t width) {
     uint32_t R = (uint32_t)(dev::kScanTableStageBytes / (stride * 4u)) & ~3u;
     R = std::min(dev::kScanMaxRows, std::max(4u, R));
-    return std::min(R, 4u * (uint32_t)(dev::kScanThreads / (width / 4u)));  // four rows per consumer thread
+    return std::min(R, 4u * (uint32_t)(dev::kScanConsumers / (width / 4u)));  // four rows per consumer thread
 }
 
 static dev::ScanParams scan_params(uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width,
