@@ -83,6 +83,12 @@ int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2,
 int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay);
 int multi_group();          // queries per item
 int multi_max_range_log2(); // largest rows-per-item exponent the kernel supports
+// consumer threads of a fused work item (a compile-time tuning knob shared with
+// the kernels): they cover a row in W / VEC column chunks, one chunk each at most
+#ifndef PIR_CONSUMER_WARPS
+#define PIR_CONSUMER_WARPS 8
+#endif
+constexpr uint32_t kFusedConsumerThreads = 32u * PIR_CONSUMER_WARPS;
 
 int device_sm_count();
 int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,

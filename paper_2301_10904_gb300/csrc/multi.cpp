@@ -94,6 +94,11 @@ int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2,
         m.key_bytes = (uint32_t)key_bytes(n);
         m.range_log2 = std::min<uint32_t>(n, item_log2);
     }
+    // the kernel's consumers cover a row in W / VEC column chunks; with 32-bit
+    // loads (some table not 16-byte aligned) that caps the width lower
+    const uint32_t vec = lay.vec ? 4u : 1u;
+    for (const MultiTable& m : lay.tables)
+        if (m.width / vec > kFusedConsumerThreads) return PIR_ERR_UNSUPPORTED;
     return PIR_OK;
 }
 

@@ -94,6 +94,7 @@ int grow(Slot& s, size_t block_bytes, size_t out_words) {
         cudaFreeHost(s.h_block);
         s.d_block = s.h_block = nullptr;
         const size_t cap = std::max(block_bytes, s.block_cap * 2);
+        s.block_cap = 0;  // nothing is allocated until both allocations succeed
         cudaError_t e = cudaMalloc((void**)&s.d_block, cap);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_block, cap);
         if (e != cudaSuccess) return cuda_fail((int)e, "serve block alloc");
@@ -104,6 +105,7 @@ int grow(Slot& s, size_t block_bytes, size_t out_words) {
         cudaFreeHost(s.h_out);
         s.d_out = s.h_out = nullptr;
         const size_t cap = std::max(out_words, s.out_cap * 2);
+        s.out_cap = 0;
         cudaError_t e = cudaMalloc((void**)&s.d_out, cap * 4);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, cap * 4);
         if (e != cudaSuccess) return cuda_fail((int)e, "serve share alloc");
@@ -134,6 +136,28 @@ void retire(pir_server* srv, Slot& s) {
     srv->stats.completed += s.reqs.size();
     s.reqs.clear();
     s.busy = false;
+    srv->cv_idle.notify_all();
+}
+
+// Worker side: a batch that could not run, or failed on the device, ends its
+// requests with error `rc` (their callers see it from pir_poll / the replay).
+void fail_batch(pir_server* srv, const std::vector<uint32_t>& batch, int rc) {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->worker_error = rc;
+    for (uint32_t id : batch) {
+        Request& r = srv->reqs[id];
+        r.status = rc;
+        r.t_done = now_ns();
+        if (r.latency_out) *r.latency_out = -1;
+        if (r.detached) {
+            r.state = kFree;
+            ++r.gen;
+            srv->free_list.push_back(id);
+        } else {
+            r.state = kDone;
+        }
+    }
+    srv->running -= (uint32_t)batch.size();
     srv->cv_idle.notify_all();
 }
 
@@ -194,8 +218,16 @@ void worker_main(pir_server* srv) {
     for (;;) {
         bool progressed = false;
         for (Slot& s : srv->slots) {
-            if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
+            if (!s.busy) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaSuccess) {
                 retire(srv, s);
+                progressed = true;
+            } else if (q != cudaErrorNotReady) {
+                // the batch failed on the device: its requests end with an error, not a hang
+                fail_batch(srv, s.reqs, cuda_fail((int)q, "serve batch"));
+                s.reqs.clear();
+                s.busy = false;
                 progressed = true;
             }
         }
@@ -228,26 +260,11 @@ void worker_main(pir_server* srv) {
         }
         if (!batch.empty()) {
             const int rc = launch_batch(srv, *free_slot, batch, tables, lay);
-            std::lock_guard<std::mutex> lock(srv->mu);
             if (rc != PIR_OK) {
                 // the batch cannot run: fail its requests rather than hang their callers
-                srv->worker_error = rc;
-                for (uint32_t id : batch) {
-                    Request& r = srv->reqs[id];
-                    r.status = rc;
-                    r.t_done = now_ns();
-                    if (r.latency_out) *r.latency_out = -1;
-                    if (r.detached) {
-                        r.state = kFree;
-                        ++r.gen;
-                        srv->free_list.push_back(id);
-                    } else {
-                        r.state = kDone;
-                    }
-                }
-                srv->running -= (uint32_t)batch.size();
-                srv->cv_idle.notify_all();
+                fail_batch(srv, batch, rc);
             } else {
+                std::lock_guard<std::mutex> lock(srv->mu);
                 srv->stats.batches += 1;
                 srv->stats.batched_queries += batch.size();
             }

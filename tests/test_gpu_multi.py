@@ -136,6 +136,20 @@ def test_multi_bad_key_sets_status_and_zero_share(env):
         assert np.array_equal(got[q], orc.answer(keys[q], Ts[assign[q]]))
 
 
+def test_multi_refuses_widths_its_consumers_cannot_cover(env):
+    """A table that is not 16-byte aligned puts the kernel on 32-bit loads, and
+    then a row of more than 256 words would be left to no consumer: the
+    planner refuses it instead of returning zero shares."""
+    torch, pir, _ = env
+    wide = torch.zeros((64, 301), dtype=torch.int32, device="cuda")  # 301 words: not a multiple of 4
+    narrow = torch.zeros((64, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(pir.PirError) as e:
+        pir.pir_multi_plan_create([narrow, wide], [0, 1])
+    assert e.value.code == -8
+    ok = torch.zeros((64, 300), dtype=torch.int32, device="cuda")  # 16-byte rows: 75 chunks of 4 words
+    pir.pir_multi_plan_create([narrow, ok], [0, 1]).close()
+
+
 def test_multi_table_full_size_zipf_mix(env):
     """8 tables, rows 2^16..2^22, widths {16,32,32,64,64,128,32,16} words, 2048
     queries Zipf(1.1) over the table order, in the bench's launch
