@@ -1024,6 +1024,37 @@ def run_reference(args):
                 list(ex.map(lambda tk: oracle.answer(tk[1], tables[tk[0]]), keys))
             return len(qs) / (time.perf_counter() - t0), threads, len(qs), time.perf_counter() - t0
         rows = width = None
+    elif args.workload == "serving_hotfull":
+        # one request per step: its Q_hot hot-table and Q_full full-table queries (oracle keys)
+        full_rows, width = wl.HOTFULL_FULL
+        rows = full_rows
+        z = wl.ZipfRows(wk["seed"], full_rows)
+        hot_rows = z.top(wl.HOTFULL_HOT_ROWS)
+        full_np = wl.table_u32(wk["seed"] * 100, full_rows, width)
+        hot_np = np.ascontiguousarray(full_np[hot_rows.astype(np.int64)])
+        nh, nf = wl.domain_bits(hot_rows.size), wl.domain_bits(full_rows)
+
+        def one_step(i):
+            from concurrent.futures import ThreadPoolExecutor
+
+            import oracle
+
+            threads = os.cpu_count() or 1
+            wanted = z.sample(wk["seed"] + 1 + i, wl.HOTFULL_WANTED)
+            ha, hb, fa, fb, _ = oracle.hotfull_plan(full_rows, hot_rows, wanted, wl.HOTFULL_Q_HOT,
+                                                    wl.HOTFULL_Q_FULL)
+            jobs = []
+            for s_, (a, b) in enumerate(zip(ha, hb)):
+                r0, r1, c0 = wl.key_randomness(wk["seed"] + 31 * i + s_, nh, 1)[0]
+                jobs.append((hot_np, oracle.gen(nh, a, b, r0, r1, c0)[0]))
+            for s_, (a, b) in enumerate(zip(fa, fb)):
+                r0, r1, c0 = wl.key_randomness(wk["seed"] + 31 * i + 100 + s_, nf, 1)[0]
+                jobs.append((full_np, oracle.gen(nf, a, b, r0, r1, c0)[0]))
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda tk: oracle.answer(tk[1], tk[0]), jobs))
+            wall = time.perf_counter() - t0
+            return len(jobs) / wall, min(threads, len(jobs)), len(jobs), wall
     elif args.workload == "pbr_1m":
         rows, width, bin_rows = wk["rows"], wk["width"], wk["bin_rows"]
         table_np = wl.table_u32(wk["seed"], rows, width)

@@ -812,7 +812,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const Mult
             h->out = q != kNoQuery ? mp.out + mp.out_off[q] : nullptr;
         }
         __syncthreads();
-        run_item<kMaxGroup, VEC, false, false>(p, w.range << tb.range_log2);
+        const uint64_t r0 = w.range << tb.range_log2;
+        switch (w.group) {  // uniform over the CTA
+            case 1: run_item<1, VEC, false, false>(p, r0); break;
+            case 2: run_item<2, VEC, false, false>(p, r0); break;
+            case 4: run_item<4, VEC, false, false>(p, r0); break;
+            default: run_item<kMaxGroup, VEC, false, false>(p, r0); break;
+        }
     }
 }
 

@@ -52,7 +52,7 @@ struct MultiTable {  // device copy of one registered table
 };
 struct MultiItem {  // (table, row range, up to 8 queries of that table)
     uint32_t table;
-    uint32_t pad;
+    uint32_t group;  // query slots of the item: 1, 2, 4 or 8 (the queries in q[0..group))
     uint64_t range;  // first row = range << range_log2
     uint32_t q[8];   // query indices, kNoQuery for empty slots
 };

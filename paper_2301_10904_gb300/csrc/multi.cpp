@@ -123,16 +123,18 @@ int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay) {
         const auto& qs = per_table[t];
         if (qs.empty()) continue;
         const uint64_t ranges = ((lay.tables[t].rows - 1) >> lay.tables[t].range_log2) + 1;
-        const size_t groups = (qs.size() + G - 1) / G;
         for (uint64_t rg = 0; rg < ranges; ++rg) {
-            for (size_t gi = 0; gi < groups; ++gi) {
+            // groups of G queries; a last, smaller group gets the smallest power of two
+            // of slots that holds it, so its item spreads over all of the CTA's producers
+            for (size_t first = 0; first < qs.size(); first += (size_t)G) {
+                const size_t left = std::min<size_t>((size_t)G, qs.size() - first);
+                uint32_t g = 1;
+                while (g < left) g <<= 1;
                 MultiItem it{};
                 it.table = (uint32_t)t;
+                it.group = g;
                 it.range = rg;
-                for (int s = 0; s < 8; ++s) {
-                    const size_t idx = gi * G + s;
-                    it.q[s] = (s < G && idx < qs.size()) ? qs[idx] : kNoQuery;
-                }
+                for (int s = 0; s < 8; ++s) it.q[s] = ((uint32_t)s < g && (size_t)s < left) ? qs[first + s] : kNoQuery;
                 lay.items.push_back(it);
             }
         }
