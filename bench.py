@@ -226,6 +226,35 @@ def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float =
     return queries / wall, min(threads, queries), queries, wall
 
 
+def oracle_one_core_qps(rows: int, seed: int, table_np, prf: int = 0, max_s: float = 6.0):
+    """The oracle on one host thread: queries per second over a few queries (at most ~max_s)."""
+    import oracle
+
+    oracle.build()
+    n = wl.domain_bits(rows)
+    queries = max(1, min(8, int(max_s / (1.7e-6 * (1 << n)))))
+    rnd = wl.key_randomness(seed + 2, n, queries)
+    alphas = wl.alphas(seed + 2, rows, queries)
+    keys = [oracle.gen(n, int(a), 1, r0, r1, c0, prf)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    t0 = time.perf_counter()
+    for k in keys:
+        oracle.answer(k, table_np)
+    return queries / (time.perf_counter() - t0), queries
+
+
+def host_cpu_model() -> str:
+    """The host CPU as the OS names it (model name, or the Arm part number)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "CPU part"):
+        for line in info.splitlines():
+            if line.lower().startswith(key.lower()):
+                return f"{key}: {line.split(':', 1)[1].strip()}"
+    return "unknown"
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def kernel_source_digest() -> str:
@@ -413,11 +442,14 @@ class SingleTableWorkload:
         return res
 
     def cpu_baseline(self):
-        qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, self.table.cpu().numpy().view(np.uint32),
-                                          prf=self.prf)
+        table_np = self.table.cpu().numpy().view(np.uint32)
+        qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, table_np, prf=self.prf)
+        one, n1 = oracle_one_core_qps(self.rows, self.seed, table_np, prf=self.prf)
         return {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
                 "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
-                          f"{cores} host threads, {wall:.1f} s wall"}
+                          f"{cores} host threads, {wall:.1f} s wall",
+                "one_core": {"value": round(one, 4), "sample": f"{n1} queries on one thread"},
+                "nproc": os.cpu_count(), "cpu": host_cpu_model()}
 
 
 class MultiTableWorkload:
