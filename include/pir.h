@@ -240,14 +240,16 @@ int pir_server_eval_noalloc(const pir_table* t, const uint8_t* keys, size_t batc
  * tables of uneven sizes and widths (batched execution, Sec. 3.2.1, across
  * tables).  Holds a device-resident work list: items of (table, row range of
  * 2^r rows, up to 8 queries of that table), r = min(ceil(log2 rows),
- * item_log2).  Keys and shares of the batch are laid out back to back in
+ * item_log2), or with item_log2 = 0 chosen per table for its queries.  Keys and shares of the batch are laid out back to back in
  * query order; pir_multi_plan_layout reports the offsets. */
 typedef struct pir_multi_plan pir_multi_plan;
 
 /* tables: host array of `ntables` descriptors (device data, every width
  * <= 512 words); table_of_key: host array, table index of each of the
- * `batch` queries; item_log2: rows per work item as a power of two, 0 for
- * the largest the kernel supports (15).  The tables must stay resident
+ * `batch` queries; item_log2: rows per work item as a power of two (at most
+ * 15), or 0 to let the planner choose per table: a cost model of dependent
+ * tree levels against work per item, given the table's query count (a lone
+ * query on a large table gets up to 2^18-row items).  The tables must stay resident
  * while the plan is used.  Allocates device memory for the work list (the
  * plan owns it).  Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN, PIR_ERR_UNSUPPORTED
  * (width), PIR_ERR_NOMEM, PIR_ERR_CUDA. */
@@ -313,7 +315,7 @@ typedef struct pir_server_config {
     uint32_t max_inflight;         /* admitted but unfinished queries; 0 = derived from the budget */
     uint64_t device_memory_budget; /* bytes of key, share and work-list space behind max_inflight; 0 = 256 MiB */
     uint32_t streams;              /* batches in flight at once, 1..8; 0 = 2 */
-    uint32_t item_log2;            /* rows per work item as a power of two; 0 = 15 */
+    uint32_t item_log2;            /* rows per work item as a power of two; 0 = per table per batch (see pir_multi_plan_create) */
 } pir_server_config;
 
 typedef struct pir_server_stats {

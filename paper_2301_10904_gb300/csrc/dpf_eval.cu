@@ -976,6 +976,12 @@ int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* s
 int multi_group() { return dev::kMaxGroup; }
 int multi_max_range_log2() { return log_sq(dev::kMaxGroup) + dev::kMaxDfsDepth; }
 
+int plan_range_log2(uint64_t rows, uint32_t n, uint32_t group, uint32_t nqg) {
+    const int lsq = log_sq(group);
+    return pick_range_log2(0, rows, n, group, nqg, std::min((int)n, lsq + 1), std::min((int)n, lsq + dev::kMaxDfsDepth),
+                           std::max(1, device_sm_count()));
+}
+
 int launch_multi(const MultiParams& mp, bool vec, void* stream) {
     if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
     if (mp.nitems == 0) return PIR_OK;

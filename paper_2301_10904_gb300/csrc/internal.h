@@ -78,11 +78,15 @@ struct MultiLayout {
     std::vector<uint64_t> key_off, out_off;
     uint64_t key_total = 0, out_total = 0;
     bool vec = true;
+    bool auto_range = false;  // rows per item chosen per table from its queries (item_log2 == 0)
 };
 int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2, MultiLayout& lay);
 int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay);
 int multi_group();          // queries per item
 int multi_max_range_log2(); // largest rows-per-item exponent the kernel supports
+// rows per item (log2) from the fused planner's cost model for one table of
+// `rows` rows with nqg groups of `group` query slots
+int plan_range_log2(uint64_t rows, uint32_t n, uint32_t group, uint32_t nqg);
 // consumer threads of a fused work item (a compile-time tuning knob shared with
 // the kernels): they cover a row in W / VEC column chunks, one chunk each at most
 #ifndef PIR_CONSUMER_WARPS

@@ -3,9 +3,11 @@
 // and CUDA-graph capture of that launch.
 //
 // The planner groups each table's queries by eights and cuts the table into
-// row ranges of 2^r rows, one work item per (range, group).  Every table gets
-// the same rows per item where it can (2^item_log2, clipped to the table), so
-// items cost about the same and the kernel's item counter balances the rest.
+// row ranges of 2^r rows, one work item per (range, group).  With an explicit
+// item_log2 every table gets the same rows per item where it can (2^item_log2,
+// clipped to the table), so items cost about the same and the kernel's item
+// counter balances the rest; with item_log2 = 0 each table's r comes from the
+// fused planner's cost model for its own queries (few queries: larger items).
 // Items of one table range are adjacent, so the items in flight at any moment
 // share table rows through L2.
 #include <cuda_runtime.h>
@@ -71,6 +73,7 @@ int upload(T** dst, const std::vector<T>& src) {
 int describe_tables(const pir_table* tables, size_t ntables, uint32_t item_log2, MultiLayout& lay) {
     const int G = multi_group();
     const int rmax = multi_max_range_log2();
+    lay.auto_range = item_log2 == 0;
     if (item_log2 == 0) item_log2 = (uint32_t)rmax;
     if ((int)item_log2 > rmax) return PIR_ERR_UNSUPPORTED;
     lay.tables.assign(ntables, MultiTable{});
@@ -122,6 +125,14 @@ int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay) {
     for (size_t t = 0; t < ntables; ++t) {
         const auto& qs = per_table[t];
         if (qs.empty()) continue;
+        if (lay.auto_range) {
+            // the table's largest slot count bounds its rows per item (a subtree is at
+            // most kMaxDfsDepth levels deep); the cost model picks within that bound
+            uint32_t gmax = 1;
+            while (gmax < (uint32_t)G && gmax < qs.size()) gmax <<= 1;
+            lay.tables[t].range_log2 = (uint32_t)plan_range_log2(
+                lay.tables[t].rows, lay.tables[t].n, gmax, (uint32_t)((qs.size() + G - 1) / G));
+        }
         const uint64_t ranges = ((lay.tables[t].rows - 1) >> lay.tables[t].range_log2) + 1;
         for (uint64_t rg = 0; rg < ranges; ++rg) {
             // groups of G queries; a last, smaller group gets the smallest power of two
