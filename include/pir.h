@@ -83,13 +83,23 @@ typedef struct pir_table {
     uint64_t stride;      /* words between consecutive rows, >= width */
 } pir_table;
 
+/* How a single-table evaluation runs: the fused kernel (expansion and product
+ * in one launch, Sec. 3.2.4), or expansion into stream-ordered scratch followed
+ * by the streaming table scan (Sec. 3.2.2's level-by-level strategy; the
+ * faster one on GB300 for a lone query on a large table). */
+#define PIR_STRATEGY_FUSED 0u
+#define PIR_STRATEGY_EXPAND_SCAN 1u
+
 /* Launch shape of the fused kernel.  `group` queries share one CTA and one
- * pass over each table tile; each CTA covers 2^range_log2 consecutive rows. */
+ * pass over each table tile; each CTA covers 2^range_log2 consecutive rows.
+ * strategy PIR_STRATEGY_EXPAND_SCAN ignores group/range_log2/vec (the
+ * expansion is planned on its own) and needs 16-byte rows with stride <= 1024. */
 typedef struct pir_plan {
     uint32_t group;      /* queries per CTA: 1, 2, 4 or 8 */
     uint32_t range_log2; /* log2 rows per CTA, 1 <= range_log2 <= n */
     uint32_t vec;        /* table words per load: 4 (128-bit) or 1 */
     uint32_t ctas;       /* resulting grid size (output of pir_plan_for) */
+    uint32_t strategy;   /* PIR_STRATEGY_FUSED or PIR_STRATEGY_EXPAND_SCAN */
 } pir_plan;
 
 /* ---- keys (host only) ----------------------------------------------- */
@@ -190,12 +200,12 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
  * bytes, 16-byte aligned.  dout: device, batch x width words, overwritten.
  * dstatus: optional device word; PIR_STATUS_BAD_KEY is OR-ed into it when a
  * key fails validation on the device, and that query's share is 0.
- * Strategy: the fused kernel, except for a single query against a table of
- * 256 MiB or more with 16-byte rows (stride <= 1024), which is expanded into
- * stream-ordered scratch of rows x 4 bytes from the library's pool and
- * contracted by the streaming scan (Sec. 3.2.2's level-by-level strategy;
- * faster there on GB300).  Same result bit for bit.  Asynchronous on
- * `stream`. */
+ * Strategy: the autotuned one for this shape (pir_autotune), else the fused
+ * kernel, except for a single query against a table of 256 MiB or more with
+ * 16-byte rows (stride <= 1024), which is expanded into stream-ordered
+ * scratch of batch x rows x 4 bytes from the library's pool and contracted by
+ * the streaming scan (PIR_STRATEGY_EXPAND_SCAN; faster there on GB300).  Same
+ * result bit for bit.  Asynchronous on `stream`. */
 int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                            uint32_t* dstatus, void* stream);
 
@@ -417,14 +427,16 @@ int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const p
  * device (heuristic, or the autotuned entry when one is cached). */
 int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
 
-/* Autotuner of the fused path's launch shape (the paper tunes batch and
- * strategy per table size, Sec. 3.2.1 and 3.2.5): times the fused kernel on
- * this table and batch (device keys dkeys, device shares dout; synchronizes
- * `stream`) for query groups G in {8,4,2,1} and rows per item 2^r around the
- * heuristic's choice, and remembers the fastest for (device, rows, width,
- * batch rounded up to a power of two); pir_server_eval*, pir_plan_for and
- * pir_server_eval_noalloc use it from then on.  Returns it in *plan and its
- * time per launch in *best_ms (optional). */
+/* Autotuner of the single-table strategy and launch shape (the paper tunes
+ * batch and strategy per table size, Sec. 3.2.1 and 3.2.5): times, on this
+ * table and batch (device keys dkeys, device shares dout; synchronizes
+ * `stream`), the fused kernel for query groups G in {8,4,2,1} and rows per
+ * item 2^r around the heuristic's choice, and, where the layout allows it and
+ * batch <= 8, the expand-and-scan strategy; remembers the fastest for
+ * (device, rows, width, batch rounded up to a power of two).
+ * pir_server_eval, pir_server_eval_device and pir_plan_for use it from then
+ * on (pir_server_eval_noalloc always runs the fused kernel on its own plan).  Returns it in *plan and its time per launch in
+ * *best_ms (optional). */
 int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
                  pir_plan* plan, float* best_ms);
 

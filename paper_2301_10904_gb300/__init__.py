@@ -52,9 +52,13 @@ class pir_server_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+PIR_STRATEGY_FUSED = 0
+PIR_STRATEGY_EXPAND_SCAN = 1
+
+
 class pir_plan(ctypes.Structure):
     _fields_ = [("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32), ("vec", ctypes.c_uint32),
-                ("ctas", ctypes.c_uint32)]
+                ("ctas", ctypes.c_uint32), ("strategy", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

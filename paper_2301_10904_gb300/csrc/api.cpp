@@ -161,16 +161,28 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     if (n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_DOMAIN;
     if (row_lo + shard->rows > (1ull << n)) return PIR_ERR_DOMAIN;
     const bool v = vec_ok(shard);
-    if (!plan_in && batch == 1 && row_lo == 0 && (uint64_t)shard->rows * shard->width * 4u >= kTwoPassMinBytes &&
-        v && shard->stride <= 1024)  // the scan engine's layout (its scratch is 16-byte aligned, ld % 4 == 0)
-        return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
+    // the scan engine's layout (its scratch is 16-byte aligned with ld % 4 == 0)
+    const bool two_ok = row_lo == 0 && v && shard->stride <= 1024;
     pir_plan plan{};
+    bool have = false;
     if (plan_in) {
         plan = *plan_in;
+        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN) {
+            if (!two_ok) return PIR_ERR_UNSUPPORTED;
+            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
+        }
+        if (plan.strategy != PIR_STRATEGY_FUSED) return PIR_ERR_ARG;
         int rc = plan_check(plan, n, shard->width, v);
         if (rc != PIR_OK) return rc;
-    } else if (row_lo != 0 || !tuned_plan(shard->rows, shard->width, batch, v, &plan) ||
-               plan_check(plan, n, shard->width, v) != PIR_OK) {
+        have = true;
+    } else if (row_lo == 0 && tuned_plan(shard->rows, shard->width, batch, v, &plan)) {
+        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN && two_ok)
+            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
+        have = plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK;
+    }
+    if (!have) {
+        if (two_ok && batch == 1 && (uint64_t)shard->rows * shard->width * 4u >= kTwoPassMinBytes)
+            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
         int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
         if (rc != PIR_OK) return rc;
     }
@@ -216,7 +228,12 @@ int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan) {
     const uint32_t n = pir_domain_bits(rows);
     if (n == 0) return PIR_ERR_DOMAIN;
     if (pir::tuned_plan(rows, width, batch, width % 4 == 0, plan)) return PIR_OK;
-    return pir::plan_fused(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, plan);
+    const int rc = pir::plan_fused(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, plan);
+    // the untuned choice of pir_server_eval_device for an aligned table of this shape
+    if (rc == PIR_OK && batch == 1 && width % 4 == 0 && width <= 1024 &&
+        rows * (uint64_t)width * 4u >= pir::kTwoPassMinBytes)
+        plan->strategy = PIR_STRATEGY_EXPAND_SCAN;
+    return rc;
 }
 
 int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
@@ -266,6 +283,25 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
         }
         if (rc != PIR_OK) break;
         if (g == 1) break;
+    }
+    // the expand-and-scan strategy, where the scan engine takes this layout
+    if (rc == PIR_OK && batch <= 8 && v && t->stride <= 1024) {
+        rc = eval_two_pass(t, n, dkeys, batch, dout, nullptr, stream);  // warm-up
+        if (rc == PIR_OK) {
+            cudaEventRecord(a, s);
+            for (int i = 0; i < 3 && rc == PIR_OK; ++i) rc = eval_two_pass(t, n, dkeys, batch, dout, nullptr, stream);
+            cudaEventRecord(b, s);
+            cudaError_t e = cudaEventSynchronize(b);
+            if (rc == PIR_OK && e != cudaSuccess) rc = cuda_fail((int)e, "autotune sync");
+            float ms = 0.f;
+            if (rc == PIR_OK) cudaEventElapsedTime(&ms, a, b);
+            ms /= 3.f;
+            if (rc == PIR_OK && (best_t < 0.f || ms < best_t)) {
+                best_t = ms;
+                best = base;
+                best.strategy = PIR_STRATEGY_EXPAND_SCAN;
+            }
+        }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -129,6 +129,36 @@ def test_autotuned_plan_is_used_and_exact(env):
         assert np.array_equal(got[q], orc.answer(ks0[q], T))
 
 
+def test_autotuner_weighs_expand_and_scan_for_few_queries(env):
+    """For a few queries the autotuner also times the expand-and-scan strategy;
+    whichever it keeps, pir_plan_for reports it and the evaluation equals the
+    oracle.  An explicit plan of either strategy gives the same shares."""
+    torch, pir, orc = env
+    rows, width, batch = 1 << 18, 64, 2
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(45, rows, width)
+    alphas = wl.alphas(45, rows, batch)
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 45)
+    table = dev_table(torch, T)
+    dk = dev_keys(torch, ks0)
+    out = torch.empty((batch, width), dtype=torch.int32, device="cuda")
+    plan, ms = pir.pir_autotune(table, dk, batch, out)
+    assert ms > 0 and plan.strategy in (pir.PIR_STRATEGY_FUSED, pir.PIR_STRATEGY_EXPAND_SCAN)
+    chosen = pir.pir_plan_for(rows, width, batch)
+    assert (chosen.strategy, chosen.group, chosen.range_log2) == (plan.strategy, plan.group, plan.range_log2)
+    got = run_device(torch, pir, table, ks0, width)
+    for q in range(batch):
+        assert np.array_equal(got[q], orc.answer(ks0[q], T))
+    fused = pir.pir_plan_for(rows, width, batch)
+    fused.strategy = pir.PIR_STRATEGY_FUSED
+    scan = pir.pir_plan_for(rows, width, batch)
+    scan.strategy = pir.PIR_STRATEGY_EXPAND_SCAN
+    if fused.group > batch:
+        fused.group = 2
+    assert np.array_equal(run_device(torch, pir, table, ks0, width, plan=fused), got)
+    assert np.array_equal(run_device(torch, pir, table, ks0, width, plan=scan), got)
+
+
 def test_host_entry_point_host_and_device_outputs(env):
     torch, pir, orc = env
     rows, width, batch = 5000, 8, 6
