@@ -268,6 +268,24 @@ int pir_multi_plan_create(const pir_table* tables, size_t ntables, const uint32_
 
 void pir_multi_plan_destroy(pir_multi_plan* plan);
 
+/* One work item of a multi-table plan, as the planner lays it out. */
+typedef struct pir_work_item {
+    uint32_t table;      /* table index */
+    uint32_t group;      /* query slots: 1, 2, 4 or 8 */
+    uint32_t range_log2; /* the table's rows per item, log2 */
+    uint32_t pad;
+    uint64_t range;      /* first row = range << range_log2 */
+    uint32_t query[8];   /* query indices (query[s] for s < group; 0xffffffff for an empty slot) */
+} pir_work_item;
+
+/* The work items pir_multi_plan_create would build for these arguments,
+ * computed on the host only (no device memory, no device needed; with no
+ * device visible the planner assumes one SM).  *nitems gets the count; if
+ * items is non-NULL, up to `capacity` items are written.  Errors as
+ * pir_multi_plan_create, without the device ones. */
+int pir_multi_plan_inspect(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                           uint32_t item_log2, pir_work_item* items, size_t capacity, uint64_t* nitems);
+
 /* Layout of a plan's batch (all outputs optional, host): key_offsets[q]
  * (bytes) and out_offsets[q] (u32 words) for q < batch, the key buffer's
  * total bytes, the share buffer's total words, the number of work items. */

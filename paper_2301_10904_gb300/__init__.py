@@ -56,6 +56,11 @@ PIR_STRATEGY_FUSED = 0
 PIR_STRATEGY_EXPAND_SCAN = 1
 
 
+class pir_work_item(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_uint32), ("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("range", ctypes.c_uint64), ("query", ctypes.c_uint32 * 8)]
+
+
 class pir_plan(ctypes.Structure):
     _fields_ = [("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32), ("vec", ctypes.c_uint32),
                 ("ctas", ctypes.c_uint32), ("strategy", ctypes.c_uint32)]
@@ -100,6 +105,9 @@ def _load():
         "pir_multi_plan_create": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, vp, ctypes.c_size_t,
                                                  ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
         "pir_multi_plan_destroy": (None, [vp]),
+        "pir_multi_plan_inspect": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, vp, ctypes.c_size_t,
+                                                  ctypes.c_uint32, vp, ctypes.c_size_t,
+                                                  ctypes.POINTER(ctypes.c_uint64)]),
         "pir_multi_plan_layout": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(ctypes.c_uint64),
                                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "pir_server_eval_multi": (ctypes.c_int, [vp, u8p, u32p, u32p, vp]),
@@ -360,6 +368,32 @@ def pir_device_status(clear: bool = False) -> int:
     flags = ctypes.c_uint32(0)
     _check(_lib.pir_device_status(ctypes.byref(flags), int(clear)), "pir_device_status")
     return flags.value
+
+
+def pir_multi_plan_inspect(tables, table_of_key, item_log2: int = 0):
+    """The planner's work items for these tables and queries, on the host.
+    `tables` are (rows, width) pairs or (rows, width, stride, aligned) tuples
+    (no memory is touched: data pointers are fake, 16-byte aligned when
+    `aligned`).  Returns a list of dicts (table, group, range_log2, range,
+    queries)."""
+    import numpy as np
+
+    descs = []
+    for t in tables:
+        rows, width = t[0], t[1]
+        stride = t[2] if len(t) > 2 else width
+        aligned = t[3] if len(t) > 3 else True
+        descs.append(pir_table(4096 if aligned else 4100, rows, width, stride))
+    arr = (pir_table * len(descs))(*descs)
+    tok = np.ascontiguousarray(table_of_key, dtype=np.uint32)
+    n = ctypes.c_uint64()
+    _check(_lib.pir_multi_plan_inspect(arr, len(descs), tok.ctypes.data, tok.size, item_log2, None, 0,
+                                       ctypes.byref(n)), "pir_multi_plan_inspect")
+    items = (pir_work_item * max(1, n.value))()
+    _check(_lib.pir_multi_plan_inspect(arr, len(descs), tok.ctypes.data, tok.size, item_log2, items, n.value,
+                                       ctypes.byref(n)), "pir_multi_plan_inspect")
+    return [{"table": w.table, "group": w.group, "range_log2": w.range_log2, "range": w.range,
+             "queries": [q for q in w.query[:w.group] if q != 0xFFFFFFFF]} for w in items[:n.value]]
 
 
 def _tables_array(tables):

@@ -157,6 +157,32 @@ int plan_items(const uint32_t* table_of_key, size_t batch, MultiLayout& lay) {
 
 extern "C" {
 
+int pir_multi_plan_inspect(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
+                           uint32_t item_log2, pir_work_item* items, size_t capacity, uint64_t* nitems) {
+    using namespace pir;
+    if (!tables || ntables == 0 || ntables > 0xffffffffu || !table_of_key || batch == 0 || batch > 0xfffffffeu ||
+        !nitems)
+        return PIR_ERR_ARG;
+    MultiLayout lay;
+    int rc = describe_tables(tables, ntables, item_log2, lay);
+    if (rc == PIR_OK) rc = plan_items(table_of_key, batch, lay);
+    if (rc != PIR_OK) return rc;
+    *nitems = lay.items.size();
+    if (items) {
+        for (size_t i = 0; i < lay.items.size() && i < capacity; ++i) {
+            const MultiItem& m = lay.items[i];
+            pir_work_item& w = items[i];
+            w.table = m.table;
+            w.group = m.group;
+            w.range_log2 = lay.tables[m.table].range_log2;
+            w.pad = 0;
+            w.range = m.range;
+            for (int q = 0; q < 8; ++q) w.query[q] = m.q[q];
+        }
+    }
+    return PIR_OK;
+}
+
 int pir_multi_plan_create(const pir_table* tables, size_t ntables, const uint32_t* table_of_key, size_t batch,
                           uint32_t item_log2, pir_multi_plan** out_plan) {
     using namespace pir;
