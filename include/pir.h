@@ -55,6 +55,7 @@ extern "C" {
 #define PIR_ERR_TIMEOUT (-6)     /* a bounded wait ran out */
 #define PIR_ERR_BUSY (-7)        /* admission refused (serving) */
 #define PIR_ERR_UNSUPPORTED (-8) /* shape outside the kernels' limits */
+#define PIR_ERR_CANCELLED (-9)   /* the request was cancelled before it ran (serving) */
 
 #define PIR_STATUS_BAD_KEY 1u    /* device status bit: some key failed validation */
 #define PIR_STATUS_SMEM_LAYOUT 2u /* device status bit: a kernel found its shared memory at an
@@ -349,6 +350,7 @@ typedef struct pir_server_config {
 typedef struct pir_server_stats {
     uint64_t submitted, completed, rejected, batches, batched_queries;
     uint32_t max_inflight;
+    uint64_t cancelled;
 } pir_server_stats;
 
 /* Starts the worker thread on the current device.  cfg may be NULL. */
@@ -384,6 +386,12 @@ int pir_server_stats_get(pir_server* server, pir_server_stats* stats);
 int pir_server_replay(pir_server* server, const double* arrival_s, const uint32_t* table_ids, const uint8_t* keys,
                       const uint64_t* key_offsets, size_t count, uint32_t* outs, const uint64_t* out_offsets,
                       int64_t* latency_ns, double* elapsed_s);
+
+/* Withdraws a submitted request that has not been batched yet: its ticket is
+ * released and its output buffer is not written.  Returns PIR_OK when it was
+ * cancelled, PIR_ERR_BUSY when it is already running or done (poll it as
+ * usual), PIR_ERR_ARG for an unknown ticket. */
+int pir_cancel(pir_server* server, uint64_t ticket);
 
 /* Drains, stops the worker and frees the server's buffers. */
 void pir_server_destroy(pir_server* server);
@@ -463,6 +471,15 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
  * bits of the current device (synchronous) and clears them if `clear`. */
 #define PIR_FAULT_WAIT_TIMEOUT 1u
 int pir_device_status(uint32_t* flags, int clear);
+
+/* Diagnostic of the bounded waits on the current device: runs a one-thread
+ * kernel that waits on an mbarrier nothing ever completes, for at most
+ * `polls` try_wait polls, so that the bound runs out as a stuck copy's would.
+ * The kernel sets PIR_FAULT_WAIT_TIMEOUT in the device status and returns;
+ * the context stays usable.  Synchronizes `stream`.  Returns PIR_ERR_TIMEOUT
+ * when the wait ran out as designed, PIR_OK if it did not (it cannot), or a
+ * CUDA error. */
+int pir_selftest_bounded_wait(uint32_t polls, void* stream);
 
 /* Human-readable name of an error code (static string). */
 const char* pir_error_string(int code);

@@ -21,7 +21,7 @@ PIR_OK = 0
 PIR_STATUS_BAD_KEY = 1
 PIR_STATUS_SMEM_LAYOUT = 2
 ERRORS = {-1: "PIR_ERR_ARG", -2: "PIR_ERR_DOMAIN", -3: "PIR_ERR_KEY", -4: "PIR_ERR_NOMEM", -5: "PIR_ERR_CUDA",
-          -6: "PIR_ERR_TIMEOUT", -7: "PIR_ERR_BUSY", -8: "PIR_ERR_UNSUPPORTED"}
+          -6: "PIR_ERR_TIMEOUT", -7: "PIR_ERR_BUSY", -8: "PIR_ERR_UNSUPPORTED", -9: "PIR_ERR_CANCELLED"}
 
 
 class PirError(RuntimeError):
@@ -46,7 +46,8 @@ class pir_server_config(ctypes.Structure):
 
 class pir_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
-                ("batches", ctypes.c_uint64), ("batched_queries", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32)]
+                ("batches", ctypes.c_uint64), ("batched_queries", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("cancelled", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -122,6 +123,8 @@ def _load():
         "pir_server_register_table": (ctypes.c_int, [vp, ctypes.POINTER(pir_table), ctypes.POINTER(ctypes.c_uint32)]),
         "pir_submit": (ctypes.c_int, [vp, ctypes.c_uint32, u8p, u32p, ctypes.POINTER(ctypes.c_uint64)]),
         "pir_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
+        "pir_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "pir_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, vp]),
         "pir_server_drain": (ctypes.c_int, [vp, ctypes.c_uint32]),
         "pir_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(pir_server_stats)]),
         "pir_server_replay": (ctypes.c_int, [vp, vp, vp, u8p, vp, ctypes.c_size_t, u32p, vp, vp,
@@ -363,6 +366,12 @@ def pir_contract_u32(dshares, batch: int, table, dout, engine: int = PIR_CONTRAC
     return dout
 
 
+def pir_selftest_bounded_wait(polls: int = 1 << 12, stream=None) -> int:
+    """Runs the bounded-wait diagnostic; returns the library's code
+    (PIR_ERR_TIMEOUT, -6, when the wait ran out as designed)."""
+    return _lib.pir_selftest_bounded_wait(polls, _stream(stream))
+
+
 def pir_device_status(clear: bool = False) -> int:
     """Library-wide device fault bits of the current device (PIR_FAULT_*)."""
     flags = ctypes.c_uint32(0)
@@ -526,6 +535,15 @@ class Server:
             return None
         _check(rc, "pir_poll")
         return lat.value
+
+    def cancel(self, ticket: int) -> bool:
+        """True when the request was withdrawn before it ran; False when it is
+        already running or done (poll it as usual)."""
+        rc = _lib.pir_cancel(self.handle, ticket)
+        if rc == -7:
+            return False
+        _check(rc, "pir_cancel")
+        return True
 
     def drain(self, timeout_ms: int = 60000):
         _check(_lib.pir_server_drain(self.handle, timeout_ms), "pir_server_drain")

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+    subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl",
                            "-Xlinker", f"-rpath,{os.path.join(CUDA_HOME, 'lib64')}"])
     os.replace(tmp, LIB)
     return LIB

@@ -125,6 +125,7 @@ constexpr uint64_t kTwoPassMinBytes = 256ull << 20;
 
 static int eval_two_pass(const pir_table* t, uint32_t n, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                          uint32_t* dstatus, void* stream) {
+    NvtxRange range("pir: expand + scan");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const uint64_t ld = (t->rows + 3) & ~3ull;
     cudaMemPool_t pool = nullptr;
@@ -199,6 +200,7 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     req.batch = (uint32_t)batch;
     req.dout = dout;
     req.dstatus = dstatus;
+    NvtxRange range("pir: fused launch");
     return launch_fused(req, plan, stream);
 }
 
@@ -217,6 +219,7 @@ const char* pir_error_string(int code) {
         case PIR_ERR_TIMEOUT: return "timed out";
         case PIR_ERR_BUSY: return "busy";
         case PIR_ERR_UNSUPPORTED: return "unsupported shape";
+        case PIR_ERR_CANCELLED: return "cancelled";
         default: return "unknown error";
     }
 }
@@ -240,6 +243,7 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
                  pir_plan* best_plan, float* best_ms) {
     using namespace pir;
     if (!table_ok(t) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu || !best_plan) return PIR_ERR_ARG;
+    NvtxRange range("pir_autotune");
     const uint32_t n = pir_domain_bits(t->rows);
     if (n == 0) return PIR_ERR_DOMAIN;
     const bool v = vec_ok(t);
@@ -340,6 +344,7 @@ int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dk
                         uint32_t* dstatus, void* stream) {
     using namespace pir;
     if (!table_ok(t) || !dkeys || !dout || bin_rows < 2) return PIR_ERR_ARG;
+    NvtxRange range("pir_server_eval_pbr");
     if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
     if (!vec_ok(t)) return PIR_ERR_UNSUPPORTED;
     const uint32_t n = pir_domain_bits(bin_rows);
@@ -420,6 +425,11 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
     return launch_materialise(req, plan, dshares, ld, stream);
 }
 
+int pir_selftest_bounded_wait(uint32_t polls, void* stream) {
+    if (polls == 0) return PIR_ERR_ARG;
+    return pir::selftest_bounded_wait(polls, stream);
+}
+
 int pir_device_status(uint32_t* flags, int clear) {
     if (!flags) return PIR_ERR_ARG;
     return pir::device_faults(flags, clear != 0);
@@ -436,6 +446,7 @@ int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const p
 
 int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream) {
     using namespace pir;
+    NvtxRange range("pir_server_eval");
     if (!table_ok(t) || !keys || !out || batch == 0) return PIR_ERR_ARG;
     const uint32_t n = pir_domain_bits(t->rows);
     if (n == 0) return PIR_ERR_DOMAIN;

@@ -7,6 +7,8 @@
 
 #include "pir.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace pir {
 
 // ---- host AES-128 (aes_host.cpp) -------------------------------------------
@@ -118,8 +120,19 @@ int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint3
 bool scan_bins_supported(const uint32_t* table, uint64_t stride, uint32_t width, uint64_t bin_rows);
 int launch_scan_bins(const uint32_t* shares, const uint32_t* table, uint64_t stride, uint32_t width, uint64_t rows,
                      uint64_t bin_rows, uint32_t* out, void* stream);
+// diagnostic: a bounded wait that must run out (scan.cu)
+int selftest_bounded_wait(uint32_t polls, void* stream);
 // library-wide device fault bits (PIR_FAULT_*), read on the current device
 int device_faults(uint32_t* flags, bool clear);
+
+// A named range of the calling host thread for timeline tools (Nsight Systems
+// and the like); without a tool attached the push and pop do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // error bookkeeping (api.cpp)
 int cuda_fail(int cuda_error_code, const char* what);

@@ -215,6 +215,7 @@ int pir_keygen_batch(uint32_t n, size_t count, const uint64_t* alphas, const uin
     if (prf != PIR_PRF_AES128 && prf != PIR_PRF_CHACHA20) return PIR_ERR_ARG;
     for (size_t i = 0; i < count; ++i)
         if ((alphas[i] >> n) != 0) return PIR_ERR_DOMAIN;
+    NvtxRange range("pir_keygen_batch");
     // one 32-byte seed per key, drawn in key order from the master seed's stream
     uint8_t master[32];
     if (seed) {

@@ -238,6 +238,7 @@ int pir_server_eval_multi(const pir_multi_plan* plan, const uint8_t* dkeys, uint
                           void* stream) {
     using namespace pir;
     if (!plan || !dkeys || !dout || (reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+    NvtxRange range("pir_server_eval_multi");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(dout, 0, plan->out_total * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_counter, 0, sizeof(uint64_t), s);
@@ -258,6 +259,7 @@ int pir_server_eval_multi(const pir_multi_plan* plan, const uint8_t* dkeys, uint
 int pir_server_eval_multi_host(pir_multi_plan* plan, const uint8_t* keys, uint32_t* out, void* stream) {
     using namespace pir;
     if (!plan || !keys || !out) return PIR_ERR_ARG;
+    NvtxRange range("pir_server_eval_multi_host");
     if (!plan->d_stage_keys) {
         cudaError_t e = cudaMalloc((void**)&plan->d_stage_keys, std::max<uint64_t>(16, plan->key_total));
         if (e == cudaSuccess)
@@ -327,6 +329,7 @@ int pir_multi_autotune(const pir_table* tables, size_t ntables, const uint32_t* 
                        float* best_ms) {
     using namespace pir;
     if (!best_item_log2) return PIR_ERR_ARG;
+    NvtxRange range("pir_multi_autotune");
     const int rmax = multi_max_range_log2();
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t a = nullptr, b = nullptr;

@@ -251,7 +251,37 @@ __global__ void __launch_bounds__(kScanThreads, 3) contract_scan_kernel(const Sc
     }
 }
 
+// Diagnostic: one thread waits on an mbarrier that expects an arrival nobody
+// makes; the bounded wait gives up after `polls` polls and records it, exactly
+// as a scan consumer whose copy never lands would.
+__global__ void wait_selftest_kernel(uint32_t polls, uint32_t* gave_up) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool done = false;
+    for (uint32_t i = 0; i < polls && !done; ++i) done = mbar_try_wait(b, 0);
+    if (!done) atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);
+    *gave_up = done ? 0u : 1u;
+}
+
 }  // namespace dev
+
+int selftest_bounded_wait(uint32_t polls, void* stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t* d = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "selftest alloc");
+    dev::wait_selftest_kernel<<<1, 32, 0, s>>>(polls, d);
+    uint32_t gave_up = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&gave_up, d, sizeof(gave_up), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "selftest");
+    return gave_up ? PIR_ERR_TIMEOUT : PIR_OK;
+}
 
 bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width) {
     return (reinterpret_cast<uintptr_t>(shares) & 15u) == 0 && ld % 4 == 0 &&

@@ -116,6 +116,7 @@ int grow(Slot& s, size_t block_bytes, size_t out_words) {
 
 // Worker side: finished batches hand their shares to the requests.
 void retire(pir_server* srv, Slot& s) {
+    NvtxRange range("serve: retire batch");
     const int64_t t = now_ns();
     std::lock_guard<std::mutex> lock(srv->mu);
     for (size_t i = 0; i < s.reqs.size(); ++i) {
@@ -164,6 +165,7 @@ void fail_batch(pir_server* srv, const std::vector<uint32_t>& batch, int rc) {
 // Worker side: packs and launches one batch on slot s.
 int launch_batch(pir_server* srv, Slot& s, const std::vector<uint32_t>& batch, const std::vector<pir_table>& tables,
                  MultiLayout& lay) {
+    NvtxRange range("serve: plan, pack and launch batch");
     std::vector<uint32_t> table_of_key(batch.size());
     for (size_t i = 0; i < batch.size(); ++i) table_of_key[i] = srv->reqs[batch[i]].table;
     int rc = describe_tables(tables.data(), tables.size(), srv->cfg.item_log2, lay);
@@ -389,6 +391,26 @@ int pir_poll(pir_server* srv, uint64_t ticket, int64_t* latency_ns) {
     ++r.gen;
     srv->free_list.push_back(idx);
     return status;
+}
+
+int pir_cancel(pir_server* srv, uint64_t ticket) {
+    if (!srv) return PIR_ERR_ARG;
+    const uint32_t idx = (uint32_t)ticket, gen = (uint32_t)(ticket >> 32);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (idx >= srv->reqs.size()) return PIR_ERR_ARG;
+    Request& r = srv->reqs[idx];
+    if (r.gen != gen || r.state == kFree || r.detached) return PIR_ERR_ARG;
+    if (r.state != kPending) return PIR_ERR_BUSY;  // already in a batch, or done
+    auto it = std::find(srv->pending.begin(), srv->pending.end(), idx);
+    if (it == srv->pending.end()) return PIR_ERR_BUSY;
+    srv->pending.erase(it);
+    r.state = kFree;
+    r.status = PIR_ERR_CANCELLED;
+    ++r.gen;
+    srv->free_list.push_back(idx);
+    srv->stats.cancelled += 1;
+    srv->cv_idle.notify_all();
+    return PIR_OK;
 }
 
 int pir_server_drain(pir_server* srv, uint32_t timeout_ms) {

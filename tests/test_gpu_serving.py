@@ -133,3 +133,64 @@ def test_poisson_replay_reconstructs_every_row(env):
         rec = ((shares[0][o:o + w].astype(np.uint64) + shares[1][o:o + w]) & M32).astype(np.uint32)
         assert np.array_equal(rec, Ts[t][alphas[q]]), q
     srv.close()
+
+
+def test_serving_mix_at_full_size():
+    """The serving workload's four resident tables (2^18 x 64, 2^20 x 32,
+    2^22 x 32, 2^24 x 16 words; 1.73 GB) in the server's own launch
+    configuration: 256 Poisson queries, table uniform per query, both servers;
+    every query reconstructs its row, eight queries give the same share alone
+    as in the mix, and one sampled query per table matches the oracle."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    import __graft_entry__ as g
+
+    g.build()
+    import oracle as orc
+    import paper_2301_10904_gb300 as pir
+
+    shapes = wl.SERVING_TABLES
+    tables = [wl.table_u32_torch(700 + i, r, w, "cuda") for i, (r, w) in enumerate(shapes)]
+    ns = [pir.pir_domain_bits(r) for r, _ in shapes]
+    count = 256
+    assign = wl.uniform_tables(701, len(shapes), count).tolist()
+    rng = np.random.Generator(np.random.PCG64(701))
+    alphas = [int(rng.integers(0, shapes[t][0])) for t in assign]
+    pairs = [pir.pir_keygen(ns[t], a, 1, bytes([q % 256, q // 256]) * 16) for q, (t, a) in enumerate(zip(assign, alphas))]
+    widths = np.array([shapes[t][1] for t in assign], np.uint64)
+    ooff = np.concatenate([[0], np.cumsum(widths)[:-1]]).astype(np.uint64)
+    klens = np.array([len(p[0]) for p in pairs], np.uint64)
+    koff = np.concatenate([[0], np.cumsum(klens)[:-1]]).astype(np.uint64)
+    srv = pir.Server(max_batch=2048, streams=2)
+    tids = [srv.register_table(t) for t in tables]
+    outs = []
+    for party in (0, 1):
+        keys = b"".join(p[party] for p in pairs)
+        o = np.zeros(int(widths.sum()), np.uint32)
+        srv.replay(wl.poisson_arrivals(702, 3000, count), [tids[t] for t in assign], keys, koff, o, ooff)
+        outs.append(o)
+    rec = ((outs[0].astype(np.uint64) + outs[1]) & M32).astype(np.uint32)
+    for q in range(count):
+        o, w = int(ooff[q]), int(widths[q])
+        want = tables[assign[q]][alphas[q]].cpu().numpy().view(np.uint32)
+        assert np.array_equal(rec[o:o + w], want), q
+    # the same share alone as in the mix
+    picks = [next(q for q in range(count) if assign[q] == t) for t in range(len(shapes))]
+    picks += [next(q for q in range(count - 1, -1, -1) if assign[q] == t) for t in range(len(shapes))]
+    for q in picks:
+        alone = np.zeros(int(widths[q]), np.uint32)
+        _wait(srv, srv.submit(tids[assign[q]], pairs[q][0], alone), timeout=60.0)
+        assert np.array_equal(alone, outs[0][int(ooff[q]):int(ooff[q]) + int(widths[q])]), q
+    srv.close()
+    # one query per table against the oracle (the 2^24-row expansion takes the oracle ~30 s)
+    host = [t.cpu().numpy().view(np.uint32) for t in tables]
+    sample = picks[:len(shapes)]
+    with ThreadPoolExecutor(max(1, min(len(sample), os.cpu_count() or 1))) as ex:
+        got = list(ex.map(lambda q: orc.answer(pairs[q][0], host[assign[q]]), sample))
+    for q, want in zip(sample, got):
+        assert np.array_equal(outs[0][int(ooff[q]):int(ooff[q]) + int(widths[q])], want), q
