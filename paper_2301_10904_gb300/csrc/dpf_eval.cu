@@ -919,9 +919,9 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     const uint32_t nqg = (batch + g - 1) / g;
     const int lsq = log_sq(g);
     const int sms = std::max(1, device_sm_count());
-    // every producer gets a subtree (r >= log2(512/G) + 1), subtrees at most kMaxDfsDepth deep
-    const int r = pick_range_log2(row_lo, rows, n, g, nqg, std::min((int)n, lsq + 1),
-                                  std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
+    // subtrees at most kMaxDfsDepth deep; below r = log2(512/G) + 1 fewer than all producers
+    // get a subtree, which a latency-bound item (one query, a small table) can afford
+    const int r = pick_range_log2(row_lo, rows, n, g, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
     pl.range_log2 = (uint32_t)r;
     const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
     pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
@@ -978,7 +978,7 @@ int multi_max_range_log2() { return log_sq(dev::kMaxGroup) + dev::kMaxDfsDepth; 
 
 int plan_range_log2(uint64_t rows, uint32_t n, uint32_t group, uint32_t nqg) {
     const int lsq = log_sq(group);
-    return pick_range_log2(0, rows, n, group, nqg, std::min((int)n, lsq + 1), std::min((int)n, lsq + dev::kMaxDfsDepth),
+    return pick_range_log2(0, rows, n, group, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth),
                            std::max(1, device_sm_count()));
 }
 
@@ -1014,7 +1014,7 @@ int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir
     const uint32_t nqg = (nbins + g - 1) / g;
     const int lsq = log_sq(g);
     const int sms = std::max(1, device_sm_count());
-    const int r = pick_range_log2(0, bin_rows, n, g, nqg, std::min((int)n, lsq + 1),
+    const int r = pick_range_log2(0, bin_rows, n, g, nqg, 1,
                                   std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
     pl.range_log2 = (uint32_t)r;
     pl.ctas = (uint32_t)std::min<uint64_t>(items_for(0, bin_rows, (uint32_t)r, nqg), (uint64_t)sms);
