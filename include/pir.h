@@ -92,15 +92,21 @@ typedef struct pir_table {
 #define PIR_STRATEGY_EXPAND_SCAN 1u
 
 /* Launch shape of the fused kernel.  `group` queries share one CTA and one
- * pass over each table tile; each CTA covers 2^range_log2 consecutive rows.
- * strategy PIR_STRATEGY_EXPAND_SCAN ignores group/range_log2/vec (the
- * expansion is planned on its own) and needs 16-byte rows with stride <= 1024. */
+ * pass over each table tile; each work item covers 2^range_log2 consecutive
+ * rows, and the grid (min(items, SMs) CTAs) takes items round-robin.  When
+ * the items do not fill the last round, each item of that round is cut into
+ * 2^tail_log2 pieces of 2^(range_log2 - tail_log2) rows, so that every CTA
+ * takes part in it (0: no cut; the planner picks it by its cost model).
+ * strategy PIR_STRATEGY_EXPAND_SCAN ignores group/range_log2/vec/tail_log2
+ * (the expansion is planned on its own) and needs 16-byte rows with
+ * stride <= 1024. */
 typedef struct pir_plan {
     uint32_t group;      /* queries per CTA: 1, 2, 4 or 8 */
-    uint32_t range_log2; /* log2 rows per CTA, 1 <= range_log2 <= n */
+    uint32_t range_log2; /* log2 rows per work item, 1 <= range_log2 <= n */
     uint32_t vec;        /* table words per load: 4 (128-bit) or 1 */
     uint32_t ctas;       /* resulting grid size (output of pir_plan_for) */
     uint32_t strategy;   /* PIR_STRATEGY_FUSED or PIR_STRATEGY_EXPAND_SCAN */
+    uint32_t tail_log2;  /* 0..min(3, range_log2 - 1): pieces per item of a partial last round */
 } pir_plan;
 
 /* ---- keys (host only) ----------------------------------------------- */

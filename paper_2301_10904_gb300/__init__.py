@@ -64,7 +64,7 @@ class pir_work_item(ctypes.Structure):
 
 class pir_plan(ctypes.Structure):
     _fields_ = [("group", ctypes.c_uint32), ("range_log2", ctypes.c_uint32), ("vec", ctypes.c_uint32),
-                ("ctas", ctypes.c_uint32), ("strategy", ctypes.c_uint32)]
+                ("ctas", ctypes.c_uint32), ("strategy", ctypes.c_uint32), ("tail_log2", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -179,6 +179,8 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     } else if (row_lo == 0 && tuned_plan(shard->rows, shard->width, batch, v, &plan)) {
         if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN && two_ok)
             return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
+        // tuned per power-of-two batch bucket: cut the last round for this batch
+        plan.tail_log2 = plan_tail_log2(0, shard->rows, n, plan.group, (uint32_t)batch, plan.range_log2);
         have = plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK;
     }
     if (!have) {
@@ -260,6 +262,7 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
         if (g > batch || (uint64_t)g * t->width > 4096u) continue;
         for (int r = (int)n; r >= 1; --r) {
             pir_plan pl{g, (uint32_t)r, base.vec, 0};
+            pl.tail_log2 = plan_tail_log2(0, t->rows, n, g, (uint32_t)batch, (uint32_t)r);
             if (plan_check(pl, n, t->width, v) != PIR_OK) continue;
             // keep shapes with at least one item per SM, or the whole table in one item
             const uint32_t nqg = (uint32_t)((batch + g - 1) / g);

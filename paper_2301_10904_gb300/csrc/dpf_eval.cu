@@ -91,7 +91,9 @@ struct FusedParams {
     uint64_t row_lo, row_hi;
     uint64_t stride;
     uint64_t first_range;
-    uint64_t nitems;
+    uint64_t nitems;     // (query group, row range) items at 2^range_log2 rows
+    uint64_t nfull;      // items run whole; the other nitems - nfull are cut into pieces
+    uint32_t tail_log2;  // pieces of 2^(range_log2 - tail_log2) rows per cut item
     const uint8_t* keys;
     uint32_t* out;
     uint32_t* status;
@@ -513,12 +515,12 @@ __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t
 }
 
 // One work item: the queries in the header slots (set by the caller) over the
-// 2^r rows starting at r0.  MAT = false: fused share x table product (a1-a6)
+// 2^r rows starting at r0 (1 <= r <= n).  MAT = false: fused share x table product (a1-a6)
 // with kConsumers consumer threads after the kProducers producers;
 // MAT = true: producers only, leaf shares written to each slot's `out`.
 // Ends with a barrier, so shared memory is free for the next item.
 template <int G, int VEC, bool MAT, bool BINS>
-__device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
+__device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int r) {
     constexpr int SQ = kProducers / G;
     constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
     constexpr int NT = MAT ? kProducers : kFusedThreads;
@@ -531,7 +533,7 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
     const bool producer = tid < kProducers;
     const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
     uint32_t* ybuf = reinterpret_cast<uint32_t*>(sm + kYOff);
-    const int n = (int)p.n, r = (int)p.range_log2;
+    const int n = (int)p.n;
     const int sd = min(LOG_SQ, r - 1);
     const int m = r - sd;
 
@@ -736,14 +738,30 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0) {
 }
 
 // Persistent grid over items (query group, row range), query groups fastest so
-// that items running at the same time share table rows through L2.
+// that items running at the same time share table rows through L2.  The first
+// nfull items (whole rounds of the grid) run whole; each later one is cut into
+// 2^tail_log2 pieces, so that the last round keeps every CTA busy.  Pieces with
+// the same index run side by side, again query groups fastest.
 template <int G, int VEC, bool MAT, bool BINS>
 __device__ __forceinline__ void eval_items(const FusedParams& p) {
     if (!smem_base_ok(p.status)) return;
     build_tables(threadIdx.x);
-    for (uint64_t item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+    const uint64_t rest = p.nitems - p.nfull;
+    const uint64_t total = p.nfull + (rest << p.tail_log2);
+    // rows the items cover: the evaluated rows, or a bin's rows (bins mode)
+    const uint64_t lo = BINS ? 0 : p.row_lo, hi = BINS ? p.bin_rows : p.row_hi;
+    for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        uint64_t item = it, piece = 0;
+        int r = (int)p.range_log2;
+        if (it >= p.nfull) {
+            const uint64_t j = it - p.nfull;
+            item = p.nfull + j % rest;
+            piece = j / rest;
+            r -= (int)p.tail_log2;
+        }
         const uint32_t qg = (uint32_t)(item % p.nqg);
-        const uint64_t r0 = (p.first_range + item / p.nqg) << p.range_log2;
+        const uint64_t r0 = ((p.first_range + item / p.nqg) << p.range_log2) + (piece << r);
+        if (r0 >= hi || r0 + (1ull << r) <= lo) continue;  // a piece outside the rows (uniform per CTA)
         if (threadIdx.x < G) {
             const uint32_t q = qg * G + threadIdx.x;
             QueryHdr* h = hdr_slot(threadIdx.x);
@@ -760,7 +778,7 @@ __device__ __forceinline__ void eval_items(const FusedParams& p) {
                 h->out = valid ? p.out + (uint64_t)q * p.width : nullptr;
         }
         __syncthreads();
-        run_item<G, VEC, MAT, BINS>(p, r0);
+        run_item<G, VEC, MAT, BINS>(p, r0, r);
     }
 }
 
@@ -813,11 +831,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const Mult
         }
         __syncthreads();
         const uint64_t r0 = w.range << tb.range_log2;
+        const int r = (int)tb.range_log2;
         switch (w.group) {  // uniform over the CTA
-            case 1: run_item<1, VEC, false, false>(p, r0); break;
-            case 2: run_item<2, VEC, false, false>(p, r0); break;
-            case 4: run_item<4, VEC, false, false>(p, r0); break;
-            default: run_item<kMaxGroup, VEC, false, false>(p, r0); break;
+            case 1: run_item<1, VEC, false, false>(p, r0, r); break;
+            case 2: run_item<2, VEC, false, false>(p, r0, r); break;
+            case 4: run_item<4, VEC, false, false>(p, r0, r); break;
+            default: run_item<kMaxGroup, VEC, false, false>(p, r0, r); break;
         }
     }
 }
@@ -876,21 +895,58 @@ static uint64_t items_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t n
 //   ceil(items / CTAs) x (n x kLevelNodes + G x 2^r),
 // kLevelNodes being one level's latency in units of one node's work at the
 // SM's full rate (~1.4 us against ~4.3 ns, measured on GB300).
+//
+// With static round-robin over C = min(items, SMs) CTAs, floor(items / C)
+// whole rounds leave items mod C for a last round in which the other CTAs
+// idle.  Cut into 2^s pieces of 2^(r-s) rows, those items spread over every
+// CTA at the price of one more path walk per piece:
+//   floor(items / C) x (n x kLevelNodes + G x 2^r)
+//     + ceil((items mod C) x 2^s / C) x (n x kLevelNodes + G x 2^(r-s)).
 constexpr uint64_t kLevelNodes = 320;
+constexpr int kMaxTailLog2 = 3;
+static double schedule_cost(uint64_t items, int sms, uint32_t n, uint32_t g, int r, int s) {
+    if (items == 0) return 0.0;
+    const uint64_t c = std::min<uint64_t>(items, (uint64_t)sms);
+    const double lat = (double)n * (double)kLevelNodes;
+    const uint64_t whole = s > 0 ? items / c : (items + c - 1) / c;
+    const uint64_t cut = s > 0 ? items - whole * c : 0;
+    const uint64_t tail_rounds = ((cut << s) + c - 1) / c;
+    return (double)whole * (lat + (double)g * (double)(1ull << r)) +
+           (double)tail_rounds * (lat + (double)g * (double)(1ull << (r - s)));
+}
+static int pick_tail_log2(uint64_t items, int sms, uint32_t n, uint32_t g, int r) {
+    int best = 0;
+    double best_cost = schedule_cost(items, sms, n, g, r, 0);
+    for (int s = 1; s <= std::min(kMaxTailLog2, r - 1); ++s) {
+        const double cost = schedule_cost(items, sms, n, g, r, s);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = s;
+        }
+    }
+    return best;
+}
 static int pick_range_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t g, uint32_t nqg, int r_min, int r_max,
-                           int sms) {
+                           int sms, bool tail) {
     int best = r_max;
     double best_cost = -1.0;
     for (int r = r_max; r >= r_min; --r) {
         const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
-        const double rounds = (double)((items + (uint64_t)sms - 1) / (uint64_t)sms);
-        const double cost = rounds * ((double)n * (double)kLevelNodes + (double)g * (double)(1ull << r));
+        const int s = tail ? pick_tail_log2(items, sms, n, g, r) : 0;
+        const double cost = schedule_cost(items, sms, n, g, r, s);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = r;
         }
     }
     return best;
+}
+
+uint32_t plan_tail_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t group, uint32_t batch,
+                        uint32_t range_log2) {
+    const uint32_t nqg = (batch + group - 1) / group;
+    const uint64_t items = items_for(row_lo, rows, range_log2, nqg);
+    return (uint32_t)pick_tail_log2(items, std::max(1, device_sm_count()), n, group, (int)range_log2);
 }
 
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
@@ -903,6 +959,7 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     if (r < 1 || r > (int)n) return PIR_ERR_UNSUPPORTED;
     const int sd = std::min(log_sq(plan.group), r - 1);
     if (r - sd > dev::kMaxDfsDepth) return PIR_ERR_UNSUPPORTED;
+    if (plan.tail_log2 > (uint32_t)std::min(kMaxTailLog2, r - 1)) return PIR_ERR_UNSUPPORTED;
     return PIR_OK;
 }
 
@@ -921,9 +978,10 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     const int sms = std::max(1, device_sm_count());
     // subtrees at most kMaxDfsDepth deep; below r = log2(512/G) + 1 fewer than all producers
     // get a subtree, which a latency-bound item (one query, a small table) can afford
-    const int r = pick_range_log2(row_lo, rows, n, g, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
+    const int r = pick_range_log2(row_lo, rows, n, g, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth), sms, true);
     pl.range_log2 = (uint32_t)r;
     const uint64_t items = items_for(row_lo, rows, (uint32_t)r, nqg);
+    pl.tail_log2 = (uint32_t)pick_tail_log2(items, sms, n, g, r);
     pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
     *plan = pl;
     return PIR_OK;
@@ -946,6 +1004,10 @@ static dev::FusedParams make_params(const EvalRequest& req, const pir_plan& plan
     p.range_log2 = plan.range_log2;
     p.nqg = (req.batch + plan.group - 1) / plan.group;
     p.nitems = items_for(req.row_lo, req.row_hi - req.row_lo, plan.range_log2, p.nqg);
+    // whole rounds of the grid run whole items; the rest are cut into pieces
+    const uint64_t c = std::min<uint64_t>(p.nitems, (uint64_t)std::max(1, device_sm_count()));
+    p.tail_log2 = plan.tail_log2;
+    p.nfull = plan.tail_log2 && c ? p.nitems / c * c : p.nitems;
     return p;
 }
 
@@ -979,7 +1041,7 @@ int multi_max_range_log2() { return log_sq(dev::kMaxGroup) + dev::kMaxDfsDepth; 
 int plan_range_log2(uint64_t rows, uint32_t n, uint32_t group, uint32_t nqg) {
     const int lsq = log_sq(group);
     return pick_range_log2(0, rows, n, group, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth),
-                           std::max(1, device_sm_count()));
+                           std::max(1, device_sm_count()), false);
 }
 
 int launch_multi(const MultiParams& mp, bool vec, void* stream) {
@@ -1015,9 +1077,11 @@ int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir
     const int lsq = log_sq(g);
     const int sms = std::max(1, device_sm_count());
     const int r = pick_range_log2(0, bin_rows, n, g, nqg, 1,
-                                  std::min((int)n, lsq + dev::kMaxDfsDepth), sms);
+                                  std::min((int)n, lsq + dev::kMaxDfsDepth), sms, true);
     pl.range_log2 = (uint32_t)r;
-    pl.ctas = (uint32_t)std::min<uint64_t>(items_for(0, bin_rows, (uint32_t)r, nqg), (uint64_t)sms);
+    const uint64_t items = items_for(0, bin_rows, (uint32_t)r, nqg);
+    pl.tail_log2 = (uint32_t)pick_tail_log2(items, sms, n, g, r);
+    pl.ctas = (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
     *plan = pl;
     return PIR_OK;
 }

@@ -100,6 +100,9 @@ int device_sm_count();
 int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan);
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
+// Pieces per cut item of the last, partial round (log2) for a plan's shape.
+uint32_t plan_tail_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t group, uint32_t batch,
+                        uint32_t range_log2);
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream);
 // partial batch retrieval: req.batch bins of bin_rows rows, req.row_hi = table rows
 int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir_plan* plan);

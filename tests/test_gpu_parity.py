@@ -110,6 +110,63 @@ def test_every_launch_shape_matches_oracle(env):
     assert ran >= 80
 
 
+def test_cut_last_round_matches_oracle(env):
+    # Items that do not fill the grid's last round are cut into 2^tail_log2
+    # pieces: every forced cut gives the oracle's shares, the ragged last
+    # range (pieces past the last row are skipped) included.
+    torch, pir, orc = env
+    rows, width, batch = (1 << 13) + 333, 16, 9
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(23, rows, width)
+    alphas = wl.alphas(5, rows, batch)
+    alphas[0] = rows - 1
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 78)
+    want = np.stack([orc.answer(k, T) for k in ks0])
+    table = dev_table(torch, T)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cut = 0
+    for g in (1, 2, 8):
+        for r in range(2, 9):
+            for s in range(1, min(3, r - 1) + 1):
+                plan = pir.pir_plan(g, r, 4, 0)
+                plan.tail_log2 = s
+                got = run_device(torch, pir, table, ks0, width, plan=plan)
+                assert np.array_equal(got, want), plan.as_dict()
+                items = -(-rows // (1 << r)) * -(-batch // g)
+                cut += items > sms and items % sms != 0
+    assert cut >= 10
+    plan = pir.pir_plan(1, 3, 4, 0)
+    plan.tail_log2 = 3  # pieces of 2^0 rows: outside the kernels' limits
+    with pytest.raises(pir.PirError) as e:
+        run_device(torch, pir, table, ks0, width, plan=plan)
+    assert e.value.code == -8
+
+
+def test_planner_cut_for_fused_and_expand(env):
+    # 200 queries over 2^14 + 77 rows: on 152 SMs the cost model takes items of
+    # 2^11 rows and 8 queries (225 items) and cuts the 73 of the last round in
+    # halves.  Both the fused product and the expansion equal the oracle.
+    torch, pir, orc = env
+    rows, width, batch = (1 << 14) + 77, 16, 200
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(29, rows, width)
+    alphas = wl.alphas(29, rows, batch)
+    alphas[-1] = rows - 1
+    ks0, _ = make_keys(orc, n, alphas, [1] * batch, 29)
+    plan = pir.pir_plan_for(rows, width, batch)
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        assert (plan.group, plan.range_log2, plan.tail_log2) == (8, 11, 1), plan.as_dict()
+    Y = np.stack([orc.full_eval(k, rows) for k in ks0])
+    table = dev_table(torch, T)
+    got = run_device(torch, pir, table, ks0, width)
+    assert np.array_equal(got, orc.contract(Y, T))
+    dk = dev_keys(torch, ks0)
+    S = torch.empty((batch, rows + 3), dtype=torch.int32, device="cuda")
+    pir.pir_expand_materialise(rows, dk, batch, S)
+    torch.cuda.synchronize()
+    assert np.array_equal(S.cpu().numpy().view(np.uint32)[:, :rows], Y)
+
+
 def test_autotuned_plan_is_used_and_exact(env):
     torch, pir, orc = env
     rows, width, batch = (1 << 15) + 9, 32, 12
