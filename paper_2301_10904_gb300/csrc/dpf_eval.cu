@@ -123,32 +123,43 @@ static_assert(sizeof(QueryHdr) * kMaxGroup <= kHdrBytes, "query slot headers exc
 __device__ __forceinline__ QueryHdr* hdr_slot(int g) { return reinterpret_cast<QueryHdr*>(sm + kHdrOff) + g; }
 
 // ---------------------------------------------------------------- GF(2^8)
-__device__ __forceinline__ uint32_t xtime(uint32_t a) { return ((a << 1) ^ (0x1bu & (0u - (a >> 7)))) & 0xffu; }
-
-__device__ uint32_t gf_mul(uint32_t a, uint32_t b) {
+// The AES S-box from its definition, evaluated by the compiler: S(x) is the
+// affine map of x^254, the inverse of x in GF(2^8) modulo x^8+x^4+x^3+x+1
+// (0 maps to 0).  Te0[x] holds the bytes 2S, S, S, 3S (byte 0 first): the
+// MixColumns column of S(x).
+constexpr uint32_t gf_xtime(uint32_t a) { return ((a << 1) ^ ((a & 0x80u) ? 0x1bu : 0u)) & 0xffu; }
+constexpr uint32_t gf_mul(uint32_t a, uint32_t b) {
     uint32_t p = 0;
-#pragma unroll
     for (int i = 0; i < 8; ++i) {
-        p ^= a & (0u - (b & 1u));
-        a = xtime(a);
+        if (b & 1u) p ^= a;
+        a = gf_xtime(a);
         b >>= 1;
     }
     return p;
 }
-
-// S(x) = affine(x^254); x^254 = x^2 * x^4 * ... * x^128 is the inverse in GF(2^8)
-__device__ uint32_t sbox_entry(uint32_t x) {
-    uint32_t sq = gf_mul(x, x), inv = sq;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        sq = gf_mul(sq, sq);
-        inv = gf_mul(inv, sq);
+constexpr uint32_t sbox_entry(uint32_t x) {
+    uint32_t inv = 1, base = x;
+    for (int e = 254; e; e >>= 1) {  // square-and-multiply
+        if (e & 1) inv = gf_mul(inv, base);
+        base = gf_mul(base, base);
     }
     uint32_t s = inv;
-#pragma unroll
     for (int k = 1; k <= 4; ++k) s ^= ((inv << k) | (inv >> (8 - k))) & 0xffu;
     return s ^ 0x63u;
 }
+struct Te0Table {
+    uint32_t v[256];
+};
+constexpr Te0Table make_te0() {
+    Te0Table t{};
+    for (uint32_t x = 0; x < 256; ++x) {
+        const uint32_t s = sbox_entry(x), s2 = gf_xtime(s);
+        t.v[x] = s2 | (s << 8) | (s << 16) | ((s2 ^ s) << 24);
+    }
+    return t;
+}
+static_assert(sbox_entry(0) == 0x63u && sbox_entry(1) == 0x7cu, "S-box: affine constant and the inverse of 1");
+__constant__ Te0Table kTe0 = make_te0();
 
 // ---------------------------------------------------------------- lookups
 // Te_t[x] for this lane sits at plane(t)*64K + x*256 + (t&1)*128 + 4*lane:
@@ -176,21 +187,18 @@ __device__ __forceinline__ bool smem_base_ok(uint32_t* status) {
     return false;
 }
 
+// 4 tables x 256 rows x 32 lane copies = 32768 words, four lanes' copies (16
+// bytes) per store.  blockDim.x is a multiple of 32, so a warp covers row x of
+// all four tables (its constant read is one broadcast, its store four
+// contiguous 128-byte runs).
 __device__ void build_tables(int tid) {
-    uint32_t* stage = reinterpret_cast<uint32_t*>(sm + kStackOff);  // Te0 staged in the stack area
-    if (tid < 256) {
-        const uint32_t s = sbox_entry((uint32_t)tid);
-        const uint32_t s2 = xtime(s);
-        stage[tid] = s2 | (s << 8) | (s << 16) | ((s2 ^ s) << 24);
-    }
-    __syncthreads();
-    // 4 tables x 256 rows x 32 lane copies = 32768 words
-#pragma unroll 4
-    for (int f = tid; f < 32768; f += (int)blockDim.x) {
-        const int t = f >> 13, x = (f >> 5) & 255, lane = f & 31;
-        const uint32_t v = stage[x];
+#pragma unroll 2
+    for (int f = tid; f < 8192; f += (int)blockDim.x) {
+        const int x = f >> 5, t = (f >> 3) & 3, q = f & 7;
+        const uint32_t v = kTe0.v[x];
         const uint32_t rv = t ? __funnelshift_l(v, v, 8 * t) : v;
-        *reinterpret_cast<uint32_t*>(sm + (t >> 1) * kPlaneBytes + x * 256 + (t & 1) * 128 + lane * 4) = rv;
+        *reinterpret_cast<uint4*>(sm + (t >> 1) * kPlaneBytes + x * 256 + (t & 1) * 128 + q * 16) =
+            make_uint4(rv, rv, rv, rv);
     }
     __syncthreads();
 }
@@ -719,7 +727,22 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
         const uint32_t ct = (uint32_t)(tid - kProducers);
         const uint32_t nc = W / VEC, nrg = kConsumers / nc;
         const uint32_t c = ct % nc, rg = ct / nc;
-        if (rg < nrg) {
+        if (nc < 32 && (nc & (nc - 1)) == 0) {
+            // every consumer thread is in a row group; lanes lane, lane + nc, ... of a
+            // warp hold the same words: add them across the warp first (mod 2^32)
+            for (uint32_t off = 16; off >= nc; off >>= 1)
+#pragma unroll
+                for (int a = 0; a < G; ++a)
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) acc[a][i] += __shfl_xor_sync(0xffffffffu, acc[a][i], off);
+            if ((tid & 31) < (int)nc) {
+#pragma unroll
+                for (int a = 0; a < G; ++a)
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i)
+                        if (acc[a][i]) atomicAdd(&red[a * W + c * VEC + i], acc[a][i]);
+            }
+        } else if (rg < nrg) {
 #pragma unroll
             for (int a = 0; a < G; ++a)
 #pragma unroll
@@ -737,6 +760,19 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
     __syncthreads();
 }
 
+// q = a / b, r = a % b, in 32-bit arithmetic when both fit (the 64-bit divide
+// is a long software sequence).
+__device__ __forceinline__ void divmod(uint64_t a, uint64_t b, uint64_t& q, uint64_t& r) {
+    if (((a | b) >> 32) == 0) {
+        const uint32_t q32 = (uint32_t)a / (uint32_t)b;
+        q = q32;
+        r = (uint32_t)a - q32 * (uint32_t)b;
+    } else {
+        q = a / b;
+        r = a - q * b;
+    }
+}
+
 // Persistent grid over items (query group, row range), query groups fastest so
 // that items running at the same time share table rows through L2.  The first
 // nfull items (whole rounds of the grid) run whole; each later one is cut into
@@ -745,22 +781,26 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
 template <int G, int VEC, bool MAT, bool BINS>
 __device__ __forceinline__ void eval_items(const FusedParams& p) {
     if (!smem_base_ok(p.status)) return;
-    build_tables(threadIdx.x);
+    // (the launch parameters are read before the tables are built, so that their
+    // first constant-cache misses overlap the fill)
     const uint64_t rest = p.nitems - p.nfull;
     const uint64_t total = p.nfull + (rest << p.tail_log2);
     // rows the items cover: the evaluated rows, or a bin's rows (bins mode)
     const uint64_t lo = BINS ? 0 : p.row_lo, hi = BINS ? p.bin_rows : p.row_hi;
+    build_tables(threadIdx.x);
     for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
         uint64_t item = it, piece = 0;
         int r = (int)p.range_log2;
         if (it >= p.nfull) {
-            const uint64_t j = it - p.nfull;
-            item = p.nfull + j % rest;
-            piece = j / rest;
+            uint64_t k;
+            divmod(it - p.nfull, rest, piece, k);
+            item = p.nfull + k;
             r -= (int)p.tail_log2;
         }
-        const uint32_t qg = (uint32_t)(item % p.nqg);
-        const uint64_t r0 = ((p.first_range + item / p.nqg) << p.range_log2) + (piece << r);
+        uint64_t range, qg64;
+        divmod(item, p.nqg, range, qg64);
+        const uint32_t qg = (uint32_t)qg64;
+        const uint64_t r0 = ((p.first_range + range) << p.range_log2) + (piece << r);
         if (r0 >= hi || r0 + (1ull << r) <= lo) continue;  // a piece outside the rows (uniform per CTA)
         if (threadIdx.x < G) {
             const uint32_t q = qg * G + threadIdx.x;
