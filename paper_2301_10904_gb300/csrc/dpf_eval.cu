@@ -267,6 +267,40 @@ __device__ __forceinline__ void prf2(const uint32_t lane4, const uint32_t lane4h
     }
 }
 
+// One child alone, c_b = AES_v(b || 0^120): the key schedule and one block
+// (200 lookups against 333 for both).  For the dependent levels, where a node
+// is expanded on its own and its thread's instruction stream is the latency:
+// the path to an item's range needs only the child on the path, and a split
+// level with few nodes gives each child its own thread.
+__device__ __forceinline__ void key_round(uint32_t lane4, uint32_t lane4h, uint32_t& k0, uint32_t& k1, uint32_t& k2,
+                                          uint32_t& k3, uint32_t rc) {
+    k0 ^= SBG(LKT(k3, 1, 2), LKT(k3, 2, 3), LKT(k3, 3, 0), LKT(k3, 0, 1)) ^ rc;
+    k1 ^= k0;
+    k2 ^= k1;
+    k3 ^= k2;
+}
+__device__ __forceinline__ uint4 prf1(uint32_t lane4, uint32_t lane4h, const uint4 v, uint32_t b) {
+    uint32_t k0 = v.x, k1 = v.y, k2 = v.z, k3 = v.w;
+    uint32_t s0 = k0 ^ b, s1 = k1, s2 = k2, s3 = k3;  // round 0: plaintext xor key
+    const uint32_t rcon[9] = {0x01u, 0x02u, 0x04u, 0x08u, 0x10u, 0x20u, 0x40u, 0x80u, 0x1bu};
+#pragma unroll
+    for (int rnd = 0; rnd < 9; ++rnd) {  // rounds 1..9
+        key_round(lane4, lane4h, k0, k1, k2, k3, rcon[rnd]);
+        const uint32_t t0 = LK(s0, 0) ^ LK(s1, 1) ^ LK(s2, 2) ^ LK(s3, 3) ^ k0;
+        const uint32_t t1 = LK(s1, 0) ^ LK(s2, 1) ^ LK(s3, 2) ^ LK(s0, 3) ^ k1;
+        const uint32_t t2 = LK(s2, 0) ^ LK(s3, 1) ^ LK(s0, 2) ^ LK(s1, 3) ^ k2;
+        const uint32_t t3 = LK(s3, 0) ^ LK(s0, 1) ^ LK(s1, 2) ^ LK(s2, 3) ^ k3;
+        s0 = t0;
+        s1 = t1;
+        s2 = t2;
+        s3 = t3;
+    }
+    key_round(lane4, lane4h, k0, k1, k2, k3, 0x36u);
+    // round 10: SubBytes + ShiftRows + AddRoundKey
+    return make_uint4(SBCOL(s0, s1, s2, s3) ^ k0, SBCOL(s1, s2, s3, s0) ^ k1, SBCOL(s2, s3, s0, s1) ^ k2,
+                      SBCOL(s3, s0, s1, s2) ^ k3);
+}
+
 // Both children under the ChaCha20 PRF: block 0 of ChaCha20 (RFC 8439) with
 // key v || 0^128, counter 0, nonce 0; words 0..3 are child 0, 4..7 child 1.
 #define CHACHA_QR(a, b, c, d)                                    \
@@ -326,6 +360,25 @@ __device__ __forceinline__ void expand_staged(uint32_t lane4, uint32_t lane4h, i
     const uint4* cw = staged_key(g) + (PIR_KEY_HEADER_BYTES / 16) + 4u * (d - 1) + 2u * (v.x & 1u);
     expand_with(lane4, lane4h, v, false, chacha, cw[0], cw[1], c0, c1);
 }
+
+// Child b of v at depth d (1-based) of staged key g: PRF plus the codeword
+// C_{lsb(v)}[b][d].
+__device__ __forceinline__ uint4 expand1_staged(uint32_t lane4, uint32_t lane4h, int g, uint32_t d, uint4 v, uint32_t b,
+                                                bool chacha) {
+    const uint4* cw = staged_key(g) + (PIR_KEY_HEADER_BYTES / 16) + 4u * (d - 1) + 2u * (v.x & 1u) + b;
+    uint4 c;
+    if (chacha) {  // one ChaCha20 block holds both children
+        uint4 c0, c1;
+        prf2_chacha(v, c0, c1);
+        c = b ? c1 : c0;
+    } else {
+        c = prf1(lane4, lane4h, v, b);
+    }
+    return xor4(c, cw[0]);
+}
+
+// Split levels with at most this many nodes give each child its own thread.
+constexpr int kPairNodes = 128;
 
 // Pending right sibling at relative level `lvl` (1..8) of thread `tid`.
 __device__ __forceinline__ uint4* stack_slot(int lvl, int tid) {
@@ -574,11 +627,9 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
                 prf = hw.y >> 24;
                 cwo = hw.z;
                 v = staged_key(tid)[1];
-                for (int d = 1; d <= n - r; ++d) {
+                for (int d = 1; d <= n - r; ++d) {  // only the child on the path
                     const uint32_t b = (uint32_t)(r0 >> (n - d)) & 1u;
-                    uint4 c0, c1;
-                    expand_staged(lane4, lane4h, tid, (uint32_t)d, v, prf != 0, c0, c1);
-                    v = b ? c1 : c0;
+                    v = expand1_staged(lane4, lane4h, tid, (uint32_t)d, v, b, prf != 0);
                 }
             } else if (p.status) {
                 atomicOr(p.status, PIR_STATUS_BAD_KEY);
@@ -596,7 +647,16 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
     for (int i = 0; i < sd; ++i) {
         const uint4* src = (i & 1) ? bufB : bufA;
         uint4* dst = (i & 1) ? bufA : bufB;
-        if (tid < (G << i)) {
+        if ((G << i) <= kPairNodes) {
+            if (tid < 2 * (G << i)) {  // thread 2 node + b computes child b of node (g << i) + idx
+                const int node = tid >> 1, g = node >> i;
+                const uint32_t b = (uint32_t)tid & 1u;
+                const uint4 v = src[node];
+                const QueryHdr* h = hdr_slot(g);
+                dst[2 * node + (int)b] =
+                    h->ok ? expand1_staged(lane4, lane4h, g, (uint32_t)(n - r + i + 1), v, b, h->prf != 0) : v;
+            }
+        } else if (tid < (G << i)) {
             const int g = tid >> i, idx = tid & ((1 << i) - 1);
             const uint4 v = src[tid];
             uint4 c0 = v, c1 = v;
