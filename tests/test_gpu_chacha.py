@@ -95,3 +95,34 @@ def test_chacha_multi_table_and_library_keys(env):
         rec = ((outs[0][o:o + w].astype(np.uint64) + outs[1][o:o + w]) & M32).astype(np.uint32)
         assert np.array_equal(rec, Ts[t][alphas[q]]), q
         assert np.array_equal(outs[0][o:o + w], orc.answer(pairs[q][0], Ts[t])), q
+
+
+def test_mixed_prf_every_path_and_split_shape(env):
+    # Explicit plans from whole-table items (no path walk) down to 2-row items
+    # (a 12-level path walk), every query-slot count: the dependent levels compute
+    # one child per thread for both PRFs, and a malformed key still yields a zero
+    # share and the status flag.
+    torch, pir, orc = env
+    rows, width, batch = (1 << 12) + 5, 16, 9
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(91, rows, width)
+    alphas = wl.alphas(91, rows, batch)
+    alphas[2] = rows - 1
+    ks0, _ = _keys(orc, n, alphas, [q % 2 for q in range(batch)], 91)
+    bad = bytearray(ks0[4])
+    bad[6] = 9  # party out of range
+    keys = ks0[:4] + [bytes(bad)] + ks0[5:]
+    want = [orc.answer(k, T) for k in ks0]
+    table = dev_table(torch, T)
+    ran = 0
+    for g in (1, 2, 4, 8):
+        for r in (1, 2, 4, 7, 10, n):
+            status = torch.zeros(1, dtype=torch.int32, device="cuda")
+            got = run_device(torch, pir, table, keys, width, plan=pir.pir_plan(g, r, 4, 0), status=status)
+            assert int(status.item()) & pir.PIR_STATUS_BAD_KEY, (g, r)
+            assert not got[4].any(), (g, r)
+            for q in range(batch):
+                if q != 4:
+                    assert np.array_equal(got[q], want[q]), (g, r, q)
+            ran += 1
+    assert ran == 24
