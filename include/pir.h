@@ -357,6 +357,7 @@ typedef struct pir_server_stats {
     uint64_t submitted, completed, rejected, batches, batched_queries;
     uint32_t max_inflight;
     uint64_t cancelled;
+    uint64_t grows; /* batch buffers reallocated because a batch outgrew them (sized for max_batch at start) */
 } pir_server_stats;
 
 /* Starts the worker thread on the current device.  cfg may be NULL. */

@@ -47,7 +47,7 @@ class pir_server_config(ctypes.Structure):
 class pir_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("batched_queries", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("cancelled", ctypes.c_uint64)]
+                ("cancelled", ctypes.c_uint64), ("grows", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -50,7 +50,7 @@ static bool is_device_pointer(const void* p) {
 constexpr uint64_t kStagingKeepBytes = 256ull << 20;
 constexpr int kMaxDevices = 64;
 
-static int staging_pool(cudaMemPool_t* pool) {
+int staging_pool(cudaMemPool_t* pool) {
     static std::mutex mu;
     static cudaMemPool_t pools[kMaxDevices] = {};
     int dev = 0;

@@ -62,6 +62,7 @@ struct Slot {
     uint32_t* d_out = nullptr;
     uint32_t* h_out = nullptr;        // pinned
     size_t out_cap = 0;               // words
+    std::vector<void*> retired_host;  // outgrown pinned buffers, freed with the server
     uint64_t* d_counter = nullptr;
     uint32_t* d_status = nullptr;
 };
@@ -86,30 +87,54 @@ struct pir_server {
 };
 
 namespace pir {
+
+// The library's stream-ordered allocation pool for the current device (api.cpp).
+int staging_pool(cudaMemPool_t* pool);
+
 namespace {
 
-int grow(Slot& s, size_t block_bytes, size_t out_words) {
+// Device buffer of `bytes` (stream-ordered, from the library's pool) and its
+// pinned mirror, replacing (d, h) only when both allocations succeed.  The old
+// device buffer is freed in stream order; the old pinned one is kept until the
+// server is destroyed (freeing pinned memory synchronises the whole device,
+// which would stall the batch in flight on the other streams).
+int realloc_pair(Slot& s, cudaMemPool_t pool, size_t bytes, void** d, void** h) {
+    void* nd = nullptr;
+    void* nh = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&nd, bytes, pool, s.stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&nh, bytes);
+    if (e != cudaSuccess) {
+        if (nd) cudaFreeAsync(nd, s.stream);
+        return cuda_fail((int)e, "serve buffer alloc");
+    }
+    if (*d) cudaFreeAsync(*d, s.stream);
+    if (*h) s.retired_host.push_back(*h);
+    *d = nd;
+    *h = nh;
+    return PIR_OK;
+}
+
+// Makes slot s hold a batch of block_bytes and out_words; counts reallocations.
+// Slots are sized for a full batch when the server starts, so this is rare.
+int grow(Slot& s, size_t block_bytes, size_t out_words, uint32_t* grown) {
+    *grown = 0;
+    if (block_bytes <= s.block_cap && out_words <= s.out_cap) return PIR_OK;
+    cudaMemPool_t pool = nullptr;
+    int rc = staging_pool(&pool);
+    if (rc != PIR_OK) return rc;
     if (block_bytes > s.block_cap) {
-        cudaFree(s.d_block);
-        cudaFreeHost(s.h_block);
-        s.d_block = s.h_block = nullptr;
         const size_t cap = std::max(block_bytes, s.block_cap * 2);
-        s.block_cap = 0;  // nothing is allocated until both allocations succeed
-        cudaError_t e = cudaMalloc((void**)&s.d_block, cap);
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_block, cap);
-        if (e != cudaSuccess) return cuda_fail((int)e, "serve block alloc");
+        rc = realloc_pair(s, pool, cap, (void**)&s.d_block, (void**)&s.h_block);
+        if (rc != PIR_OK) return rc;
         s.block_cap = cap;
+        ++*grown;
     }
     if (out_words > s.out_cap) {
-        cudaFree(s.d_out);
-        cudaFreeHost(s.h_out);
-        s.d_out = s.h_out = nullptr;
         const size_t cap = std::max(out_words, s.out_cap * 2);
-        s.out_cap = 0;
-        cudaError_t e = cudaMalloc((void**)&s.d_out, cap * 4);
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, cap * 4);
-        if (e != cudaSuccess) return cuda_fail((int)e, "serve share alloc");
+        rc = realloc_pair(s, pool, cap * 4, (void**)&s.d_out, (void**)&s.h_out);
+        if (rc != PIR_OK) return rc;
         s.out_cap = cap;
+        ++*grown;
     }
     return PIR_OK;
 }
@@ -177,7 +202,12 @@ int launch_batch(pir_server* srv, Slot& s, const std::vector<uint32_t>& batch, c
     const size_t o_ooff = align16(o_koff + batch.size() * sizeof(uint64_t));
     const size_t o_keys = align16(o_ooff + batch.size() * sizeof(uint64_t));
     const size_t total = align16(o_keys + lay.key_total);
-    rc = grow(s, total, lay.out_total);
+    uint32_t grown = 0;
+    rc = grow(s, total, lay.out_total, &grown);
+    if (grown) {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stats.grows += grown;
+    }
     if (rc != PIR_OK) return rc;
     std::memcpy(s.h_block + o_tab, lay.tables.data(), lay.tables.size() * sizeof(MultiTable));
     std::memcpy(s.h_block + o_items, lay.items.data(), lay.items.size() * sizeof(MultiItem));
@@ -352,6 +382,17 @@ int pir_server_create(const pir_server_config* cfg_in, pir_server** out) {
             rc = cuda_fail((int)e, "serve slot");
             break;
         }
+        // a full batch: up to 64 table descriptors, about 64 work items, a key of
+        // the widest domain and two offsets per query, and 512 share words per query
+        const size_t block = align16(64 * sizeof(MultiTable)) +
+                             (size_t)cfg.max_batch * (64 * sizeof(MultiItem) + 2 * sizeof(uint64_t) + 2592);
+        uint32_t grown = 0;
+        rc = grow(s, block, (size_t)cfg.max_batch * 512, &grown);
+        if (rc == PIR_OK) {
+            const cudaError_t se = cudaStreamSynchronize(s.stream);
+            if (se != cudaSuccess) rc = cuda_fail((int)se, "serve slot sync");
+        }
+        if (rc != PIR_OK) break;
     }
     if (rc != PIR_OK) {
         pir_server_destroy(srv);
@@ -461,11 +502,12 @@ void pir_server_destroy(pir_server* srv) {
     }
     if (srv->worker.joinable()) srv->worker.join();
     for (Slot& s : srv->slots) {
+        if (s.d_block) cudaFreeAsync(s.d_block, s.stream);
+        if (s.d_out) cudaFreeAsync(s.d_out, s.stream);
         if (s.stream) cudaStreamSynchronize(s.stream);
-        cudaFree(s.d_block);
         cudaFreeHost(s.h_block);
-        cudaFree(s.d_out);
         cudaFreeHost(s.h_out);
+        for (void* h : s.retired_host) cudaFreeHost(h);
         cudaFree(s.d_counter);
         cudaFree(s.d_status);
         if (s.done) cudaEventDestroy(s.done);

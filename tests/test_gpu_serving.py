@@ -194,3 +194,33 @@ def test_serving_mix_at_full_size():
         got = list(ex.map(lambda q: orc.answer(pairs[q][0], host[assign[q]]), sample))
     for q, want in zip(sample, got):
         assert np.array_equal(outs[0][int(ooff[q]):int(ooff[q]) + int(widths[q])], want), q
+
+
+def test_batch_buffers_presized_and_grown_in_stream_order(env):
+    # Slots are sized for max_batch queries at start: an ordinary mix does not
+    # reallocate. Tiny items (2^2 rows: up to 4,096 work items per query on the
+    # 2^14-row table) outgrow that estimate; the slots grow (stream-ordered,
+    # while the other stream's batch may run) and every share stays the oracle's.
+    torch, pir, orc, Ts, dts = env
+    for item_log2, expect_growth in ((0, False), (2, True)):
+        srv = pir.Server(max_batch=4, streams=2, item_log2=item_log2)
+        tids = [srv.register_table(t) for t in dts]
+        rng = np.random.Generator(np.random.PCG64(77 + item_log2))
+        assign = rng.integers(0, len(SHAPES), 24).tolist()
+        outs, wants = [], []
+        tickets = []
+        for q, t in enumerate(assign):
+            n = pir.pir_domain_bits(SHAPES[t][0])
+            alpha = int(rng.integers(0, SHAPES[t][0]))
+            k0, _ = make_keys(orc, n, [alpha], [1], 4000 + 100 * item_log2 + q)
+            out = np.zeros(SHAPES[t][1], np.uint32)
+            tickets.append(srv.submit(tids[t], k0[0], out))
+            outs.append(out)
+            wants.append(orc.answer(k0[0], Ts[t]))
+        for tk in tickets:
+            _wait(srv, tk, timeout=60.0)
+        st = srv.stats()
+        srv.close()
+        for q in range(len(assign)):
+            assert np.array_equal(outs[q], wants[q]), (item_log2, q)
+        assert (st["grows"] > 0) == expect_growth, st
