@@ -52,3 +52,31 @@ def test_key_size_and_domain(lib):
 def test_error_strings(lib):
     assert lib.pir_error_string(0) == "ok"
     assert lib.pir_error_string(-3) == "malformed key"
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    # Every public struct of include/pir.h, compiled by the host C compiler:
+    # size and each field's offset equal the ctypes mirror the binding uses.
+    import shutil
+    import subprocess
+
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {name: getattr(lib, name) for name in
+               ("pir_table", "pir_plan", "pir_server_config", "pir_server_stats", "pir_work_item")}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pir.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
