@@ -994,7 +994,7 @@ static uint64_t items_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t n
 // work; a CTA runs its items one after another.  Pick r minimising
 //   ceil(items / CTAs) x (n x kLevelNodes + G x 2^r),
 // kLevelNodes being one level's latency in units of one node's work at the
-// SM's full rate (~1.4 us against ~4.3 ns, measured on GB300).
+// SM's full rate (~0.75 us against ~5.9 ns, measured on GB300).
 //
 // With static round-robin over C = min(items, SMs) CTAs, floor(items / C)
 // whole rounds leave items mod C for a last round in which the other CTAs
@@ -1002,7 +1002,7 @@ static uint64_t items_for(uint64_t row_lo, uint64_t rows, uint32_t r, uint32_t n
 // CTA at the price of one more path walk per piece:
 //   floor(items / C) x (n x kLevelNodes + G x 2^r)
 //     + ceil((items mod C) x 2^s / C) x (n x kLevelNodes + G x 2^(r-s)).
-constexpr uint64_t kLevelNodes = 320;
+constexpr uint64_t kLevelNodes = 130;
 constexpr int kMaxTailLog2 = 3;
 static double schedule_cost(uint64_t items, int sms, uint32_t n, uint32_t g, int r, int s) {
     if (items == 0) return 0.0;
