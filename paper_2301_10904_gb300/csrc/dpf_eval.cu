@@ -472,6 +472,48 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
     if (rg >= nrg) return;
     const uint32_t nrows = (2u * kc) << sd;
     const uint32_t submask = (1u << sd) - 1u;
+    if (sd >= 1) {
+        // Rows in pairs (j, l), (j, l + 1) with l even: their shares of a query are adjacent words,
+        // so one 64-bit load fetches both.  UP pairs (2 UP rows) per thread are in flight.
+        constexpr int UP = G <= 2 ? 4 : 2;
+        const uint32_t npairs = nrows >> 1;
+        for (uint32_t pr0 = rg; pr0 < npairs; pr0 += UP * nrg) {
+            uint32_t tv[UP][2][VEC];
+            uint32_t yi[UP];
+            bool any[UP];
+#pragma unroll
+            for (int u = 0; u < UP; ++u) {
+                const uint32_t pr = pr0 + u * nrg;
+                const uint32_t rr = 2u * pr;
+                const uint32_t j = rr >> sd, l = rr & submask;
+                yi[u] = j * SQ + l;
+                any[u] = false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t row = r0 + ((uint64_t)(l + h) << m) + 2ull * kbase + j;
+                    const bool ok = pr < npairs && row >= p.row_lo && row < p.row_hi;
+                    any[u] |= ok;
+                    if (ok) {
+                        load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv[u][h]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) tv[u][h][i] = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UP; ++u) {
+                if (!any[u]) continue;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const uint2 y = *reinterpret_cast<const uint2*>(yb + g * 2 * kPairs * SQ + yi[u]);
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) acc[g][i] += y.x * tv[u][0][i] + y.y * tv[u][1][i];
+                }
+            }
+        }
+        return;
+    }
     constexpr int U = G <= 2 ? 8 : 4;
     for (uint32_t rr0 = rg; rr0 < nrows; rr0 += U * nrg) {
         uint32_t tv[U][VEC];
