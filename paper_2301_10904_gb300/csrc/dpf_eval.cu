@@ -457,6 +457,70 @@ __device__ __forceinline__ void bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Rows in groups of R (R = 2 or 4): rows (j, l), ..., (j, l + R - 1) with l a
+// multiple of R have adjacent shares for every query, so one 64- or 128-bit
+// load fetches a query's shares of the whole group.  Group q of the phase is
+// rows R q .. R q + R - 1 in the phase's row order (all with the same j when
+// the subtree count 2^sd is at least R); consumer (c, rg) takes groups rg,
+// rg + nrg, ..., with 8 (G <= 2) or 4 rows in flight.
+template <int G, int VEC, int R>
+__device__ __forceinline__ void mac_rows_grouped(const FusedParams& p, const uint32_t* yb, uint64_t r0, int m, int sd,
+                                                 uint32_t kbase, uint32_t nrows, uint32_t (&acc)[G][VEC], uint32_t c,
+                                                 uint32_t rg, uint32_t nrg) {
+    static_assert(R == 2 || R == 4, "rows per group");
+    constexpr int SQ = kProducers / G;
+    constexpr int UG = (G <= 2 ? 8 : 4) / R;
+    const uint32_t submask = (1u << sd) - 1u;
+    const uint32_t ngroups = nrows / R;
+    for (uint32_t q0 = rg; q0 < ngroups; q0 += UG * nrg) {
+        uint32_t tv[UG][R][VEC];
+        uint32_t yi[UG];
+        bool any[UG];
+#pragma unroll
+        for (int u = 0; u < UG; ++u) {
+            const uint32_t q = q0 + u * nrg;
+            const uint32_t rr = (uint32_t)R * q;
+            const uint32_t j = rr >> sd, l = rr & submask;
+            yi[u] = j * SQ + l;
+            any[u] = false;
+#pragma unroll
+            for (int h = 0; h < R; ++h) {
+                const uint64_t row = r0 + ((uint64_t)(l + h) << m) + 2ull * kbase + j;
+                const bool ok = q < ngroups && row >= p.row_lo && row < p.row_hi;
+                any[u] |= ok;
+                if (ok) {
+                    load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv[u][h]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) tv[u][h][i] = 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UG; ++u) {
+            if (!any[u]) continue;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                uint32_t y[R];
+                if constexpr (R == 4) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(yb + g * 2 * kPairs * SQ + yi[u]);
+                    y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
+                } else {
+                    const uint2 v = *reinterpret_cast<const uint2*>(yb + g * 2 * kPairs * SQ + yi[u]);
+                    y[0] = v.x; y[1] = v.y;
+                }
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    uint32_t a = acc[g][i];
+#pragma unroll
+                    for (int h = 0; h < R; ++h) a += y[h] * tv[u][h][i];
+                    acc[g][i] = a;
+                }
+            }
+        }
+    }
+}
+
 // Consumer thread `ct` of kConsumers: multiply the shares of leaf pairs
 // kbase..kbase+kc-1 of every subtree (buffer yb) into acc.  Consumer (c, rg)
 // owns words c*VEC..c*VEC+VEC-1 of every G query for rows rg, rg+nrg, ...;
@@ -472,46 +536,14 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
     if (rg >= nrg) return;
     const uint32_t nrows = (2u * kc) << sd;
     const uint32_t submask = (1u << sd) - 1u;
-    if (sd >= 1) {
-        // Rows in pairs (j, l), (j, l + 1) with l even: their shares of a query are adjacent words,
-        // so one 64-bit load fetches both.  UP pairs (2 UP rows) per thread are in flight.
-        constexpr int UP = G <= 2 ? 4 : 2;
-        const uint32_t npairs = nrows >> 1;
-        for (uint32_t pr0 = rg; pr0 < npairs; pr0 += UP * nrg) {
-            uint32_t tv[UP][2][VEC];
-            uint32_t yi[UP];
-            bool any[UP];
-#pragma unroll
-            for (int u = 0; u < UP; ++u) {
-                const uint32_t pr = pr0 + u * nrg;
-                const uint32_t rr = 2u * pr;
-                const uint32_t j = rr >> sd, l = rr & submask;
-                yi[u] = j * SQ + l;
-                any[u] = false;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint64_t row = r0 + ((uint64_t)(l + h) << m) + 2ull * kbase + j;
-                    const bool ok = pr < npairs && row >= p.row_lo && row < p.row_hi;
-                    any[u] |= ok;
-                    if (ok) {
-                        load_row<VEC>(p.table + (row - p.row_lo) * p.stride + (uint64_t)c * VEC, tv[u][h]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < VEC; ++i) tv[u][h][i] = 0;
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UP; ++u) {
-                if (!any[u]) continue;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const uint2 y = *reinterpret_cast<const uint2*>(yb + g * 2 * kPairs * SQ + yi[u]);
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) acc[g][i] += y.x * tv[u][0][i] + y.y * tv[u][1][i];
-                }
-            }
+    if constexpr (VEC == 4) {  // (groups of four with 32-bit table loads would spill at G = 8)
+        if (sd >= 2) {
+            mac_rows_grouped<G, VEC, 4>(p, yb, r0, m, sd, kbase, nrows, acc, c, rg, nrg);
+            return;
         }
+    }
+    if (sd >= 1) {
+        mac_rows_grouped<G, VEC, 2>(p, yb, r0, m, sd, kbase, nrows, acc, c, rg, nrg);
         return;
     }
     constexpr int U = G <= 2 ? 8 : 4;
