@@ -8,14 +8,16 @@
 //
 // Structure.  One CTA per SM (512 producer + 256 consumer threads), persistent
 // over work items; an item is G queries x 2^r consecutive rows.
-//  1. lookup tables, built once per CTA: the S-box derived from GF(2^8), the
-//     four AES column tables Te0..Te3 (Te_r = rotl(Te0, 8r)), each with 32
-//     lane-private copies so that lane l always reads bank l.  A lookup is one
-//     PRMT (forms (byte << 8) | 4l) plus one LDS; no rotations.
+//  1. lookup tables, built once per CTA from a T-table column the compiler
+//     derives (S-box from GF(2^8)): the four AES column tables Te0..Te3
+//     (Te_r = rotl(Te0, 8r)), each with 32 lane-private copies so that lane l
+//     always reads bank l.  A lookup is one PRMT (forms (byte << 8) | 4l) plus
+//     one LDS; no rotations.
 //  2. per item, path: thread g walks query g from the root to the item's
-//     range node at depth n - r (one PRF per level).
+//     range node at depth n - r (one PRF block per level: the child on the path).
 //  3. split: level by level in shared memory until each query has one subtree
-//     root per thread (SQ = 512/G threads per query).
+//     root per thread (SQ = 512/G threads per query); a thread per child while
+//     a level has few nodes.
 //  4. per-thread depth-first expansion of its subtree (the paper's
 //     memory-bounded traversal, Sec. 3.2.3), pending right siblings in a
 //     shared-memory stack: O(threads x depth) node storage, not O(L).  One
@@ -28,7 +30,9 @@
 //     G queries at once, into register accumulators against the table rows
 //     it indexes (each row read once per CTA), while the producers fill the
 //     other buffer.  Named barriers pass the buffers back and forth; the
-//     consumers have the copy engine prefetch the next phase's rows into L2.
+//     consumers read a query's shares of up to four rows with one load, and
+//     for one or two queries per item have the copy engine prefetch the next
+//     phase's rows into L2.
 //  6. accumulators are summed in shared memory and added to out with one
 //     u32 atomicAdd per (query, word); addition mod 2^32 is associative, so
 //     the result is bit-exact in any order.
@@ -523,9 +527,11 @@ __device__ __forceinline__ void mac_rows_grouped(const FusedParams& p, const uin
 
 // Consumer thread `ct` of kConsumers: multiply the shares of leaf pairs
 // kbase..kbase+kc-1 of every subtree (buffer yb) into acc.  Consumer (c, rg)
-// owns words c*VEC..c*VEC+VEC-1 of every G query for rows rg, rg+nrg, ...;
-// U rows' loads are issued before their multiply-adds (U = 8 for one or two
-// queries per item, where the scan is a large share of the work, else 4).
+// owns words c*VEC..c*VEC+VEC-1 of every G query.  With two or more subtrees
+// it takes rows in groups whose shares it loads together (mac_rows_grouped);
+// with one subtree, rows rg, rg+nrg, ..., U at a time, U rows' loads issued
+// before their multiply-adds (U = 8 for one or two queries per item, where the
+// scan is a large share of the work, else 4).
 template <int G, int VEC>
 __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* yb, uint64_t r0, int m, int sd,
                                           uint32_t kbase, uint32_t kc, uint32_t (&acc)[G][VEC], uint32_t ct) {
