@@ -382,10 +382,12 @@ int pir_server_create(const pir_server_config* cfg_in, pir_server** out) {
             rc = cuda_fail((int)e, "serve slot");
             break;
         }
-        // a full batch: up to 64 table descriptors, about 64 work items, a key of
-        // the widest domain and two offsets per query, and 512 share words per query
+        // a full batch: up to 64 table descriptors; per query up to 256 work items
+        // (the planner gives a lone query about one item per SM, 128 on 152 SMs;
+        // queries of one table share items), a key of the widest domain and two
+        // offsets; and 512 share words per query
         const size_t block = align16(64 * sizeof(MultiTable)) +
-                             (size_t)cfg.max_batch * (64 * sizeof(MultiItem) + 2 * sizeof(uint64_t) + 2592);
+                             (size_t)cfg.max_batch * (256 * sizeof(MultiItem) + 2 * sizeof(uint64_t) + 2592);
         uint32_t grown = 0;
         rc = grow(s, block, (size_t)cfg.max_batch * 512, &grown);
         if (rc == PIR_OK) {
