@@ -460,6 +460,12 @@ int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const p
  * device (heuristic, or the autotuned entry when one is cached). */
 int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
 
+/* The heuristic launch shape for (rows, width, batch) on a device with `sms`
+ * SMs (1..65536), computed on the host only (no device needed, no autotuned
+ * entry consulted): what pir_plan_for answers untuned on such a device.
+ * Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN, PIR_ERR_UNSUPPORTED (width). */
+int pir_plan_inspect(uint64_t rows, uint32_t width, size_t batch, uint32_t sms, pir_plan* plan);
+
 /* Autotuner of the single-table strategy and launch shape (the paper tunes
  * batch and strategy per table size, Sec. 3.2.1 and 3.2.5): times, on this
  * table and batch (device keys dkeys, device shares dout; synchronizes

@@ -133,6 +133,8 @@ def _load():
         "pir_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp,
                                         ctypes.POINTER(pir_plan), ctypes.POINTER(ctypes.c_float)]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
+        "pir_plan_inspect": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_uint32,
+                                            ctypes.POINTER(pir_plan)]),
         "pir_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
@@ -596,6 +598,13 @@ def pir_autotune(table, dkeys, batch: int, dout, stream=None):
 def pir_plan_for(rows: int, width: int, batch: int) -> pir_plan:
     p = pir_plan()
     _check(_lib.pir_plan_for(rows, width, batch, ctypes.byref(p)), "pir_plan_for")
+    return p
+
+
+def pir_plan_inspect(rows: int, width: int, batch: int, sms: int) -> pir_plan:
+    """The heuristic plan for a device with `sms` SMs, on the host only."""
+    p = pir_plan()
+    _check(_lib.pir_plan_inspect(rows, width, batch, sms, ctypes.byref(p)), "pir_plan_inspect")
     return p
 
 

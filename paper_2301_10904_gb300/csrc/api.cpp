@@ -228,17 +228,28 @@ const char* pir_error_string(int code) {
 
 const char* pir_last_cuda_error(void) { return pir::g_cuda_msg; }
 
-int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan) {
-    if (!plan || rows < 1 || width == 0 || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+// The untuned choice of pir_server_eval_device for an aligned table of this shape on a device with `sms` SMs.
+static int heuristic_plan(uint64_t rows, uint32_t width, size_t batch, int sms, pir_plan* plan) {
+    if (!plan || rows < 1 || width == 0 || batch == 0 || batch > 0xffffffffu || sms < 1) return PIR_ERR_ARG;
     const uint32_t n = pir_domain_bits(rows);
     if (n == 0) return PIR_ERR_DOMAIN;
-    if (pir::tuned_plan(rows, width, batch, width % 4 == 0, plan)) return PIR_OK;
-    const int rc = pir::plan_fused(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, plan);
-    // the untuned choice of pir_server_eval_device for an aligned table of this shape
+    const int rc = pir::plan_fused_sms(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, sms, plan);
     if (rc == PIR_OK && batch == 1 && width % 4 == 0 && width <= 1024 &&
         rows * (uint64_t)width * 4u >= pir::kTwoPassMinBytes)
         plan->strategy = PIR_STRATEGY_EXPAND_SCAN;
     return rc;
+}
+
+int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan) {
+    if (!plan || rows < 1 || width == 0 || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+    if (pir_domain_bits(rows) == 0) return PIR_ERR_DOMAIN;
+    if (pir::tuned_plan(rows, width, batch, width % 4 == 0, plan)) return PIR_OK;
+    return heuristic_plan(rows, width, batch, std::max(1, pir::device_sm_count()), plan);
+}
+
+int pir_plan_inspect(uint64_t rows, uint32_t width, size_t batch, uint32_t sms, pir_plan* plan) {
+    if (sms == 0 || sms > 65536) return PIR_ERR_ARG;
+    return heuristic_plan(rows, width, batch, (int)sms, plan);
 }
 
 int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,

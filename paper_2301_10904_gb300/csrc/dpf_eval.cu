@@ -1145,7 +1145,12 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
 
 int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan) {
-    if (width == 0 || batch == 0 || n == 0) return PIR_ERR_ARG;
+    return plan_fused_sms(rows, row_lo, n, width, batch, vec_ok, std::max(1, device_sm_count()), plan);
+}
+
+int plan_fused_sms(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok, int sms,
+                   pir_plan* plan) {
+    if (width == 0 || batch == 0 || n == 0 || sms < 1) return PIR_ERR_ARG;
     pir_plan pl{};
     pl.vec = (vec_ok && width % 4 == 0) ? 4 : 1;
     if (width / pl.vec > (uint32_t)dev::kMaxChunks) return PIR_ERR_UNSUPPORTED;
@@ -1155,7 +1160,6 @@ int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint3
     pl.group = g;
     const uint32_t nqg = (batch + g - 1) / g;
     const int lsq = log_sq(g);
-    const int sms = std::max(1, device_sm_count());
     // subtrees at most kMaxDfsDepth deep; below r = log2(512/G) + 1 fewer than all producers
     // get a subtree, which a latency-bound item (one query, a small table) can afford
     const int r = pick_range_log2(row_lo, rows, n, g, nqg, 1, std::min((int)n, lsq + dev::kMaxDfsDepth), sms, true);

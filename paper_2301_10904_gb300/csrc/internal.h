@@ -97,6 +97,9 @@ int plan_range_log2(uint64_t rows, uint32_t n, uint32_t group, uint32_t nqg);
 constexpr uint32_t kFusedConsumerThreads = 32u * PIR_CONSUMER_WARPS;
 
 int device_sm_count();
+// The same for a device with `sms` SMs (host only).
+int plan_fused_sms(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
+                   int sms, pir_plan* plan);
 int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan);
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
