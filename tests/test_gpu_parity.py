@@ -61,6 +61,7 @@ def run_device(torch, pir, table, keys, W, plan=None, status=None):
 SHAPES = [  # (rows, width, batch): several tiles and ragged tails
     (2, 1, 1), (3, 4, 2), (100, 3, 5), (1000, 16, 9), (4096 + 77, 16, 3), (1 << 14, 64, 8),
     ((1 << 15) + 1000, 32, 11), (1 << 12, 1, 17), (1 << 13, 100, 4), (1 << 11, 256, 8),
+    (5000, 4, 5), (3000, 8, 9),  # narrow aligned rows: one or two column chunks per consumer row group
 ]
 
 
