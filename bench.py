@@ -403,15 +403,24 @@ class SingleTableWorkload:
             con = timed(lambda: pir.pir_contract_u32(S, self.batch, self.table, m_imad, stream=stream), reps)
             mma = timed(lambda: pir.pir_contract_u32(S, self.batch, self.table, m_mma,
                                                      engine=pir.PIR_CONTRACT_MMA_U8, stream=stream), reps)
+            m_tc = torch.empty_like(self.dout)
+            tc = timed(lambda: pir.pir_contract_u32(S, self.batch, self.table, m_tc,
+                                                    engine=pir.PIR_CONTRACT_TC_F16, stream=stream), reps)
             ok_imad, ok_mma = bool(torch.equal(m_imad, self.dout)), bool(torch.equal(m_mma, self.dout))
-            exp_ms, con_ms, mma_ms = [exp], [con], [mma]
-            tot = exp + min(con, mma)
+            ok_tc = bool(torch.equal(m_tc, self.dout))
+            tot = exp + min(con, mma, tc)
+            # 10 fp16 limb products per u32 multiply-add on the tensor pipe: 2 * 10 * B * L * W flops
+            tc_flops = 2.0 * 10 * self.batch * self.rows * self.width
             out["materialised"] = {"qps": round(self.batch / (tot / 1e3), 2),
-                                   "expand_ms": round(statistics.mean(exp_ms), 4),
-                                   "contract_imad_ms": round(statistics.mean(con_ms), 4),
-                                   "contract_mma_u8_ms": round(statistics.mean(mma_ms), 4),
+                                   "expand_ms": round(exp, 4),
+                                   "contract_imad_ms": round(con, 4),
+                                   "contract_mma_u8_ms": round(mma, 4),
+                                   "contract_tc_f16_ms": round(tc, 4),
+                                   "contract_tc_f16_tflops": round(tc_flops / (tc * 1e-3) / 1e12, 1),
+                                   "contract_tc_f16_gbs": round((s_bytes + self.rows * self.width * 4)
+                                                                / (tc * 1e-3) / 1e9, 1),
                                    "share_matrix_bytes": s_bytes,
-                                   "bit_exact_vs_fused": {"imad": ok_imad, "mma_u8": ok_mma}}
+                                   "bit_exact_vs_fused": {"imad": ok_imad, "mma_u8": ok_mma, "tc_f16": ok_tc}}
             del S
         if self.args.scan and self.width % 4 == 0 and self.rows * self.width * 4 > 2 * L2_BYTES:
             out["scan"] = self.scan_roofline()

@@ -428,6 +428,7 @@ int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dk
 #define PIR_CONTRACT_IMAD 0   /* CUDA-core 32-bit multiply-add */
 #define PIR_CONTRACT_MMA_U8 1 /* tensor-core u8 x u8 -> s32 MMAs on 8-bit limbs (10 per u32 product), exact */
 #define PIR_CONTRACT_SCAN 2   /* streaming table scan for a few queries, bound by HBM bandwidth */
+#define PIR_CONTRACT_TC_F16 3 /* tcgen05 tensor cores, fp16 signed 8-bit limbs, fp32 TMEM accumulators, exact */
 
 /* Expansion only (the level-by-level strategy's output, Sec. 3.2.2): writes
  * the full share vectors dshares[q * ld + j] = Eval(k_q, j) for j < rows,
@@ -444,6 +445,15 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  * single matrix-matrix multiplication").  engine (same result bit for bit):
  *  - PIR_CONTRACT_IMAD: 64 x 64 output tiles on CUDA cores, any batch;
  *  - PIR_CONTRACT_MMA_U8: the same tiles on the tensor pipe (8-bit limbs);
+ *  - PIR_CONTRACT_TC_F16: 128-query x 64-word tiles (32 words when
+ *    t->width <= 32) on the fifth-generation tensor cores (tcgen05.mma
+ *    with accumulators in tensor memory): every u32 is split into four
+ *    signed 8-bit limbs held exactly in fp16, the ten limb products of
+ *    the low 32 bits accumulate exactly in fp32 for 256 values of k at a
+ *    time and are then folded into u32 totals.  One CTA per SM (about
+ *    200 KB of shared memory).  Its waits are bounded like the scan's;
+ *    one that gives up leaves dout incomplete and sets
+ *    PIR_FAULT_WAIT_TIMEOUT;
  *  - PIR_CONTRACT_SCAN: for a few queries, where the product is bound by
  *    reading the table (Sec. 3.2.4): the copy engine streams table rows and
  *    share words through shared memory, eight queries per pass over the

@@ -340,6 +340,7 @@ def pir_server_eval_range(shard, row_lo: int, domain_rows: int, dkeys, batch: in
 PIR_CONTRACT_IMAD = 0
 PIR_CONTRACT_MMA_U8 = 1
 PIR_CONTRACT_SCAN = 2
+PIR_CONTRACT_TC_F16 = 3
 PIR_FAULT_WAIT_TIMEOUT = 1
 
 

@@ -239,6 +239,8 @@ __global__ void __launch_bounds__(256) contract_mma_u8_kernel(const uint32_t* __
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                     uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream) {
     if (engine == PIR_CONTRACT_SCAN) return launch_scan(shares, ld, batch, table, stride, width, rows, out, stream);
+    if (engine == PIR_CONTRACT_TC_F16)
+        return launch_contract_tc(shares, ld, batch, table, stride, width, rows, out, stream);
     if (engine == PIR_CONTRACT_MMA_U8) {
         const uint32_t by = (batch + dev::kMmBM - 1) / dev::kMmBM, bz = (width + dev::kMmBN - 1) / dev::kMmBN;
         const int sms = std::max(1, device_sm_count());

@@ -1,0 +1,430 @@
+// Share matrix x table mod 2^32 on the fifth-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), exactly: the product of the
+// unfused baseline (paper Sec. 3.1: the B x L share matrix and the L x W
+// table "batched together as a single matrix-matrix multiplication"; Sec.
+// 3.2.2) for batches that make it a dense contraction.
+//
+//   out[b][w] += sum_{k < K} S[b][k] * T[k][w]   (mod 2^32)
+//
+// Exactness.  Every u32 x is split into four signed 8-bit limbs,
+// x = sum_i s_i 2^{8i} (mod 2^32) with s_i in [-128, 127]: the bytes y_i of
+// y = x + 0x80808080 (mod 2^32) give s_i = y_i - 128.  These limbs are exact
+// in fp16, and so is every limb product (|s_i t_j| <= 2^14).  Mod 2^32 the
+// product keeps the ten limb products with i + j <= 3, in four shift classes
+// d = i + j; class d accumulates in fp32 in tensor memory, where every partial
+// sum is an integer of magnitude at most (d + 1) * 2^14 * 256 <= 2^24 over 256
+// values of k, so no partial sum is rounded.  After every 256 values of k the
+// classes are drained into u32 totals (sum_d class_d << 8d) and restart from
+// zero.  (sm_103a has no integer kind of tcgen05.mma, hence fp16 limbs.)
+//
+// One CTA per (128-query x TN-word output tile, k slice), 13 warps:
+//  - warps 5-12 load 64 values of k of the S tile (128 x 64 u32) and the T
+//    tile (64 x TN u32), split them into fp16 limb planes and store the
+//    planes in shared memory in the 128-byte-swizzled K-major layout the
+//    tensor core reads; two stages with full/empty mbarriers;
+//  - one lane of warp 4 issues a stage's 40 tcgen05.mma (M = 128, N = TN,
+//    K = 16; A = a limb plane of S, B = a limb plane of T) into the class
+//    accumulators and frees the stage with tcgen05.commit;
+//  - warps 0-3 (TMEM lanes 0-127, one per query row of the tile) drain one
+//    accumulator set with tcgen05.ld while the MMAs fill the other.
+// Split-k partial tiles meet in out with u32 atomics (order-independent, so
+// bit-exact).  Every wait is bounded: one that gives up records
+// PIR_FAULT_WAIT_TIMEOUT and the CTA winds down (it waits, bounded, for its
+// own MMAs, then frees its tensor memory).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace pir {
+namespace dev {
+namespace {
+
+constexpr uint32_t kTcM = 128;              // queries per tile = TMEM lanes = MMA M
+constexpr uint32_t kTcStageK = 64;          // k per stage: one 128-byte row of fp16 per operand row
+constexpr uint32_t kTcStages = 2;
+constexpr uint32_t kTcStagesPerChunk = 4;   // 256 k between drains (the exactness bound above)
+constexpr uint32_t kTcChunkK = kTcStageK * kTcStagesPerChunk;
+constexpr uint32_t kTcDrainWarps = 4;       // warps 0-3
+constexpr uint32_t kTcMmaWarp = 4;          // allocates TMEM; its lane 0 issues the MMAs
+constexpr uint32_t kTcConvWarps = 8;        // warps 5-12
+constexpr uint32_t kTcConvThreads = 32 * kTcConvWarps;
+constexpr uint32_t kTcThreads = 32 * (kTcDrainWarps + 1 + kTcConvWarps);
+constexpr uint32_t kTcPlaneA = kTcM * 128;  // bytes of one limb plane of the S tile
+constexpr uint32_t kTcHeader = 1024;        // mbarriers, TMEM address, abort flag
+constexpr uint32_t kTcSpinLimit = 1u << 22; // polls per bounded wait (each try_wait may also suspend)
+
+// header offsets (bytes from the 1024-aligned base)
+constexpr uint32_t kTcFull = 0, kTcEmpty = 16, kTcAccFull = 32, kTcAccEmpty = 48, kTcDone = 64;
+constexpr uint32_t kTcTmemSlot = 72, kTcAbort = 76;
+
+template <int TN>
+struct TcShape {
+    static_assert(TN == 32 || TN == 64, "tile width");
+    static constexpr uint32_t kPlaneB = TN * 128;  // bytes of one limb plane of the T tile
+    static constexpr uint32_t kStageBytes = 4 * kTcPlaneA + 4 * kPlaneB;
+    static constexpr uint32_t kSmem = 1024 /* alignment slack */ + kTcHeader + kTcStages * kStageBytes;
+    static constexpr uint32_t kTmemCols = 2 * 4 * TN;  // two accumulator sets of four classes
+    // instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B f16
+    // (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits
+    // 17-22, M >> 4 at bits 24-28
+    static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((kTcM >> 4) << 24);
+    static_assert(kSmem <= 227u * 1024u, "shared memory");
+    static_assert(kTmemCols >= 32 && kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
+    static_assert(kPlaneB % 1024 == 0 && kTcPlaneA % 1024 == 0 && kTcHeader % 1024 == 0, "swizzle atoms");
+};
+
+struct TcParams {
+    const uint32_t* S;
+    uint64_t ld;
+    const uint32_t* T;
+    uint64_t stride;
+    uint64_t K;
+    uint64_t kslice;  // k per CTA, a multiple of kTcChunkK
+    uint32_t* out;
+    uint32_t* faults;  // the library's device fault word
+    uint32_t B, W;
+    uint32_t vec;  // S and T 16-byte aligned, ld and stride multiples of 4
+};
+
+extern __shared__ char tc_sm[];
+
+__device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity.  Gives up when
+// another role of the CTA has given up (abort flag), or after kTcSpinLimit
+// polls, recording the fault and raising the flag.
+__device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t* faults) {
+    for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
+        if (try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    atomicOr(faults, PIR_FAULT_WAIT_TIMEOUT);
+    *abort_flag = 1u;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// ---- tcgen05 -----------------------------------------------------------------
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in 128-byte swizzle atoms
+// (8 rows x 128 bytes, 1024-byte aligned): start address >> 4 at bits 0-13,
+// leading byte offset (unused with this swizzle) 16 >> 4 at bits 16-29,
+// stride byte offset between 8-row groups 1024 >> 4 at bits 32-45, descriptor
+// version 1 at bits 46-47, swizzle mode 128B (2) at bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on `bar` once every tcgen05 operation this thread issued before has completed
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- limb planes -------------------------------------------------------------
+__device__ __forceinline__ uint32_t sub1152(uint32_t h) {  // (1024 + y) - 1152 = y - 128, per fp16 half, exact
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(0x64806480u));
+    return r;
+}
+
+// Four consecutive values of k of one operand row -> for each limb plane p,
+// the four fp16 limbs s_p of those values (8 bytes, lowest k first).  A
+// half with bits 0x64yy is 1024 + yy.
+__device__ __forceinline__ void limbs4(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3, uint2 (&pl)[4]) {
+    const uint32_t y0 = x0 + 0x80808080u, y1 = x1 + 0x80808080u, y2 = x2 + 0x80808080u, y3 = x3 + 0x80808080u;
+    const uint32_t a_lo = __byte_perm(y0, y1, 0x5140u), a_hi = __byte_perm(y0, y1, 0x7362u);
+    const uint32_t b_lo = __byte_perm(y2, y3, 0x5140u), b_hi = __byte_perm(y2, y3, 0x7362u);
+    constexpr uint32_t C = 0x64646464u;
+    pl[0] = make_uint2(sub1152(__byte_perm(a_lo, C, 0x4140u)), sub1152(__byte_perm(b_lo, C, 0x4140u)));
+    pl[1] = make_uint2(sub1152(__byte_perm(a_lo, C, 0x4342u)), sub1152(__byte_perm(b_lo, C, 0x4342u)));
+    pl[2] = make_uint2(sub1152(__byte_perm(a_hi, C, 0x4140u)), sub1152(__byte_perm(b_hi, C, 0x4140u)));
+    pl[3] = make_uint2(sub1152(__byte_perm(a_hi, C, 0x4342u)), sub1152(__byte_perm(b_hi, C, 0x4342u)));
+}
+
+// byte offset of (row r, k quad q) in a 128-byte-swizzled K-major plane: the
+// 16-byte chunk q / 2 of row r moves to chunk (q / 2) ^ (r % 8)
+__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t q) {
+    return r * 128u + ((((q >> 1) ^ (r & 7u)) << 4) | ((q & 1u) << 3));
+}
+
+__device__ __forceinline__ void sts64(uint32_t addr, uint2 v) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(v.x), "r"(v.y) : "memory");
+}
+
+// Four consecutive words from p, of which the first `nvalid` exist (the rest
+// read as 0).  kStream: evict-first loads (the share matrix is read once).
+template <bool kStream>
+__device__ __forceinline__ uint4 load4(const uint32_t* p, uint32_t nvalid, uint32_t vec) {
+    if (vec && nvalid >= 4)
+        return kStream ? __ldcs(reinterpret_cast<const uint4*>(p)) : __ldg(reinterpret_cast<const uint4*>(p));
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (nvalid > 0) v.x = __ldg(p);
+    if (nvalid > 1) v.y = __ldg(p + 1);
+    if (nvalid > 2) v.z = __ldg(p + 2);
+    if (nvalid > 3) v.w = __ldg(p + 3);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {
+    return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
+}
+
+template <int TN>
+__global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcParams p) {
+    using Sh = TcShape<TN>;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t raw = sm_u32(tc_sm);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms are 1024-byte aligned
+    char* const gbase = tc_sm + (base - raw);
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(gbase + kTcAbort);
+    const uint32_t m0 = blockIdx.y * kTcM, n0 = blockIdx.z * (uint32_t)TN;
+    const uint64_t k0 = (uint64_t)blockIdx.x * p.kslice;
+    const uint64_t kend = k0 + p.kslice < p.K ? k0 + p.kslice : p.K;
+    const uint32_t nst = (uint32_t)((kend - k0 + kTcStageK - 1) / kTcStageK);
+    const uint32_t nch = (nst + kTcStagesPerChunk - 1) / kTcStagesPerChunk;
+
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < kTcStages; ++s) {
+            mbar_init(base + kTcFull + 8u * s, kTcConvThreads);
+            mbar_init(base + kTcEmpty + 8u * s, 1u);
+        }
+        for (uint32_t b = 0; b < 2; ++b) {
+            mbar_init(base + kTcAccFull + 8u * b, 1u);
+            mbar_init(base + kTcAccEmpty + 8u * b, 32u * kTcDrainWarps);
+        }
+        mbar_init(base + kTcDone, 1u);
+        *abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kTcMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + kTcTmemSlot),
+                     "r"(Sh::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + kTcTmemSlot);
+
+    if (warp > kTcMmaWarp) {
+        // ---- conversion warps: u32 tiles -> fp16 limb planes -------------------
+        // S tile: thread -> k quad q of rows it*16 + cw*2 + lane/16 (it < 8);
+        // T tile: thread -> k quad q of words 4*n4 .. 4*n4+3.  Half a warp
+        // covers one 128-byte plane row: conflict-free 8-byte stores.
+        const uint32_t ct = threadIdx.x - 32u * (kTcMmaWarp + 1), cw = ct >> 5;
+        const uint32_t q = lane & 15u, n4 = ct >> 4;
+        const bool has_b = n4 < (uint32_t)TN / 4u;
+        const uint32_t nw = n0 + 4u * n4;
+        const uint32_t wval = has_b && nw < p.W ? min(4u, p.W - nw) : 0u;
+        for (uint32_t g = 0; g < nst; ++g) {
+            const uint32_t s = g & 1u;
+            const uint64_t kq = k0 + (uint64_t)g * kTcStageK + 4u * q;
+            const uint32_t kval = kq < kend ? (uint32_t)(kend - kq < 4u ? kend - kq : 4u) : 0u;
+            uint4 a[8];
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const uint32_t m = m0 + it * 16u + cw * 2u + (lane >> 4);
+                a[it] = load4<true>(p.S + (uint64_t)m * p.ld + kq, m < p.B ? kval : 0u, p.vec);
+            }
+            uint4 t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) t[e] = load4<false>(p.T + (kq + e) * p.stride + nw, e < (int)kval ? wval : 0u, p.vec);
+            if (!wait_bounded(base + kTcEmpty + 8u * s, ((g >> 1) & 1u) ^ 1u, abort_flag, p.faults)) break;
+            const uint32_t stage = base + kTcHeader + s * Sh::kStageBytes;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                uint2 pl[4];
+                limbs4(a[it].x, a[it].y, a[it].z, a[it].w, pl);
+                const uint32_t off = sw128_off(it * 16u + cw * 2u + (lane >> 4), q);
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) sts64(stage + pp * kTcPlaneA + off, pl[pp]);
+            }
+            if (has_b) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint2 pl[4];
+                    limbs4(word_of(t[0], w), word_of(t[1], w), word_of(t[2], w), word_of(t[3], w), pl);
+                    const uint32_t off = sw128_off(4u * n4 + w, q);
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) sts64(stage + 4u * kTcPlaneA + pp * Sh::kPlaneB + off, pl[pp]);
+                }
+            }
+            // the tensor core reads the planes through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(base + kTcFull + 8u * s);
+        }
+    } else if (warp == kTcMmaWarp) {
+        // ---- MMA issue: 4 k-steps x 10 limb pairs per stage ------------------
+        if (lane == 0) {
+            for (uint32_t g = 0; g < nst; ++g) {
+                const uint32_t s = g & 1u, c = g / kTcStagesPerChunk, b = c & 1u;
+                const bool first = g % kTcStagesPerChunk == 0;
+                const bool last = g % kTcStagesPerChunk == kTcStagesPerChunk - 1 || g + 1 == nst;
+                if (first && !wait_bounded(base + kTcAccEmpty + 8u * b, ((c >> 1) & 1u) ^ 1u, abort_flag, p.faults))
+                    break;
+                if (!wait_bounded(base + kTcFull + 8u * s, (g >> 1) & 1u, abort_flag, p.faults)) break;
+                tc_fence_after();
+                const uint32_t stage = base + kTcHeader + s * Sh::kStageBytes;
+#pragma unroll
+                for (uint32_t t = 0; t < kTcStageK / 16; ++t) {
+#pragma unroll
+                    for (uint32_t i = 0; i < 4; ++i) {
+                        const uint64_t ad = sw128_desc(stage + i * kTcPlaneA) + 2u * t;  // + 32 bytes per k-step
+#pragma unroll
+                        for (uint32_t j = 0; i + j < 4; ++j) {
+                            const uint64_t bd = sw128_desc(stage + 4u * kTcPlaneA + j * Sh::kPlaneB) + 2u * t;
+                            // class i + j; its first MMA of a chunk (i = 0, first k-step) overwrites
+                            mma_f16(tmem + (b * 4u + i + j) * (uint32_t)TN, ad, bd, Sh::kIdesc,
+                                    (first && t == 0 && i == 0) ? 0u : 1u);
+                        }
+                    }
+                }
+                mma_commit(base + kTcEmpty + 8u * s);
+                if (last) mma_commit(base + kTcAccFull + 8u * b);
+            }
+            // every MMA issued completes before the tensor memory is freed (bounded)
+            mma_commit(base + kTcDone);
+            for (uint32_t i = 0; i < kTcSpinLimit && !try_wait(base + kTcDone, 0u); ++i) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- drain warps: class accumulators -> u32 totals of this lane's row --
+        uint32_t total[TN];
+#pragma unroll
+        for (int n = 0; n < TN; ++n) total[n] = 0u;
+        const uint32_t lane_addr = tmem + ((warp * 32u) << 16);
+        bool ok = true;
+        for (uint32_t c = 0; c < nch; ++c) {
+            const uint32_t b = c & 1u;
+            // tcgen05.ld is warp-collective: the lanes agree on whether to go on
+            ok = __all_sync(0xffffffffu, wait_bounded(base + kTcAccFull + 8u * b, (c >> 1) & 1u, abort_flag, p.faults));
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll
+            for (uint32_t d = 0; d < 4; ++d) {
+#pragma unroll
+                for (uint32_t h = 0; h < (uint32_t)TN / 32u; ++h) {
+                    uint32_t r[32];
+                    tmem_ld32(lane_addr + (b * 4u + d) * (uint32_t)TN + h * 32u, r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        total[h * 32 + e] += (uint32_t)__float2int_rn(__uint_as_float(r[e])) << (8u * d);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(base + kTcAccEmpty + 8u * b);
+        }
+        const uint32_t m = m0 + warp * 32u + lane;
+        if (ok && m < p.B) {
+#pragma unroll
+            for (int n = 0; n < TN; ++n)
+                if (n0 + n < p.W && total[n]) atomicAdd(p.out + (uint64_t)m * p.W + n0 + n, total[n]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kTcMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::kTmemCols)
+                     : "memory");
+    }
+}
+
+template <int TN>
+int launch_tc(const TcParams& p, dim3 grid, cudaStream_t s) {
+    using Sh = TcShape<TN>;
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Sh::kSmem);
+    if (e != cudaSuccess) return cuda_fail((int)e, "contract (tcgen05) attribute");
+    contract_tc_kernel<TN><<<grid, kTcThreads, Sh::kSmem, s>>>(p);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "contract (tcgen05) launch");
+}
+
+}  // namespace
+}  // namespace dev
+
+int launch_contract_tc(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                       uint32_t width, uint64_t rows, uint32_t* out, void* stream) {
+    uint32_t* faults = device_fault_word();
+    if (!faults) return cuda_fail((int)cudaGetLastError(), "device fault word");
+    const uint32_t tn = width <= 32 ? 32u : 64u;
+    const uint64_t mt = (batch + dev::kTcM - 1) / dev::kTcM, nt = (width + tn - 1) / tn;
+    const uint64_t sms = (uint64_t)std::max(1, device_sm_count());
+    // one CTA per SM: the output tiles times enough k slices to fill one wave,
+    // each slice a whole number of 256-value accumulator chunks
+    uint64_t slices = std::max<uint64_t>(1, sms / (mt * nt));
+    uint64_t kslice = (rows + slices - 1) / slices;
+    kslice = (kslice + dev::kTcChunkK - 1) / dev::kTcChunkK * dev::kTcChunkK;
+    slices = (rows + kslice - 1) / kslice;
+    if (slices > 0x7fffffffull || mt > 65535 || nt > 65535) return PIR_ERR_UNSUPPORTED;
+    dev::TcParams p;
+    p.S = shares;
+    p.ld = ld;
+    p.T = table;
+    p.stride = stride;
+    p.K = rows;
+    p.kslice = kslice;
+    p.out = out;
+    p.faults = faults;
+    p.B = batch;
+    p.W = width;
+    p.vec = (reinterpret_cast<uintptr_t>(shares) % 16 == 0 && reinterpret_cast<uintptr_t>(table) % 16 == 0 &&
+             ld % 4 == 0 && stride % 4 == 0)
+                ? 1u
+                : 0u;
+    const dim3 grid((uint32_t)slices, (uint32_t)mt, (uint32_t)nt);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return tn == 32 ? dev::launch_tc<32>(p, grid, s) : dev::launch_tc<64>(p, grid, s);
+}
+
+}  // namespace pir

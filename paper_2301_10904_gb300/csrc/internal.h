@@ -116,6 +116,10 @@ int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* s
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                     uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream);
 
+// the same product on the tcgen05 tensor cores with fp16 limbs (contract_tc.cu)
+int launch_contract_tc(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
+                       uint32_t width, uint64_t rows, uint32_t* out, void* stream);
+
 // streaming scan engine for a few queries (scan.cu): eight queries per pass
 bool scan_supported(const uint32_t* shares, uint64_t ld, const uint32_t* table, uint64_t stride, uint32_t width);
 int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
@@ -130,6 +134,8 @@ int launch_scan_bins(const uint32_t* shares, const uint32_t* table, uint64_t str
 int selftest_bounded_wait(uint32_t polls, void* stream);
 // library-wide device fault bits (PIR_FAULT_*), read on the current device
 int device_faults(uint32_t* flags, bool clear);
+// device address of that fault word on the current device (nullptr on a CUDA error)
+uint32_t* device_fault_word();
 
 // A named range of the calling host thread for timeline tools (Nsight Systems
 // and the like); without a tool attached the push and pop do nothing.

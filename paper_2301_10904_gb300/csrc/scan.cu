@@ -381,4 +381,9 @@ int device_faults(uint32_t* flags, bool clear) {
     return PIR_OK;
 }
 
+uint32_t* device_fault_word() {
+    void* p = nullptr;
+    return cudaGetSymbolAddress(&p, dev::g_device_faults) == cudaSuccess ? static_cast<uint32_t*>(p) : nullptr;
+}
+
 }  // namespace pir

@@ -58,7 +58,7 @@ def test_materialised_bad_key_gives_zero_vector_and_status(env):
     assert not got[1].any() and int(status.item()) & 1
 
 
-@pytest.mark.parametrize("engine", [0, 1], ids=["imad", "mma_u8"])
+@pytest.mark.parametrize("engine", [0, 1, 3], ids=["imad", "mma_u8", "tc_f16"])
 @pytest.mark.parametrize("B,L,W", [(1, 1, 1), (3, 100, 5), (64, 4096, 64), (70, 3000, 65), (256, 1 << 14, 16),
                                    (5, 777, 128), (9, 20000, 32)])
 def test_contract_matches_oracle(env, B, L, W, engine):
@@ -93,14 +93,57 @@ def test_materialised_pipeline_equals_fused_and_oracle(env):
         pir.pir_contract_u32(S, batch, table, mat)
         mma = torch.empty_like(mat)
         pir.pir_contract_u32(S, batch, table, mma, engine=pir.PIR_CONTRACT_MMA_U8)
+        tc = torch.empty_like(mat)
+        pir.pir_contract_u32(S, batch, table, tc, engine=pir.PIR_CONTRACT_TC_F16)
         fused = torch.empty_like(mat)
         pir.pir_server_eval_device(table, dk, batch, fused)
         torch.cuda.synchronize()
         m = mat.cpu().numpy().view(np.uint32)
         assert np.array_equal(m, fused.cpu().numpy().view(np.uint32))
         assert torch.equal(mma, mat)
+        assert torch.equal(tc, mat)
         for q in (0, batch - 1):
             assert np.array_equal(m[q], orc.answer(keys[q], T))
         outs.append(m)
     rec = (outs[0].astype(np.uint64) + outs[1]) & M32
     assert np.array_equal(rec.astype(np.uint32), T[alphas])
+
+
+def _tc_contract(torch, pir, S, T, pad=0):
+    B, L = S.shape
+    Sd = torch.zeros((B, L + pad), dtype=torch.int32)
+    Sd[:, :L] = torch.from_numpy(S.view(np.int32))
+    out = torch.full((B, T.shape[1]), 5, dtype=torch.int32, device="cuda")
+    pir.pir_contract_u32(Sd.cuda()[:, :L], B, dev_table(torch, T), out, engine=pir.PIR_CONTRACT_TC_F16)
+    torch.cuda.synchronize()
+    flags = pir.pir_device_status(clear=True)
+    assert flags == 0, flags
+    return out.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("B,L,W,pad", [
+    (200, (1 << 16) + 77, 48, 0),   # 2 query tiles, several 256-k accumulator chunks per CTA, ragged k tail
+    (129, 5000, 96, 0),             # one row in the second query tile; two word tiles, the second ragged
+    (128, 20000, 32, 0),            # the 32-word tile shape
+    (37, 3001, 33, 2),              # unaligned rows (ld % 4 != 0: scalar loads), ragged everywhere
+    (300, 256, 64, 0),              # exactly one chunk per CTA
+])
+def test_tc_contract_matches_oracle(env, B, L, W, pad):
+    torch, pir, orc = env
+    rng = np.random.Generator(np.random.PCG64(B * 7 + L + W))
+    S = rng.integers(0, 1 << 32, (B, L), dtype=np.uint64).astype(np.uint32)
+    T = wl.table_u32(W + 1, L, W)
+    assert np.array_equal(_tc_contract(torch, pir, S, T, pad), orc.contract(S, T))
+
+
+def test_tc_contract_exact_at_the_accumulator_bound(env):
+    """0x7F7F7F80 splits into four signed limbs of -128, so every limb product
+    is +2^14 and a class-3 accumulator reaches 4 * 2^14 * 256 = 2^24 just
+    before it is drained: the largest value the exactness argument allows."""
+    torch, pir, orc = env
+    B, L, W = 130, 76 * 512 + 37, 40  # three 256-k chunks per CTA
+    S = np.full((B, L), 0x7F7F7F80, dtype=np.uint32)
+    T = np.full((L, W), 0x7F7F7F80, dtype=np.uint32)
+    S[3, :] = 0x80808080  # limbs of mixed sign in one row
+    T[:, 7] = 0xFFFFFFFF
+    assert np.array_equal(_tc_contract(torch, pir, S, T), orc.contract(S, T))
