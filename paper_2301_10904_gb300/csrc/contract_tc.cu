@@ -56,6 +56,7 @@ constexpr uint32_t kTcPlaneA = kTcM * 128;  // bytes of one limb plane of the S 
 constexpr uint32_t kTcHeader = 1024;        // mbarriers, TMEM address, abort flag
 constexpr uint32_t kTcSpinLimit = 1u << 22; // polls per bounded wait (each try_wait may also suspend)
 
+
 // header offsets (bytes from the 1024-aligned base)
 constexpr uint32_t kTcFull = 0, kTcEmpty = 16, kTcAccFull = 32, kTcAccEmpty = 48, kTcDone = 64;
 constexpr uint32_t kTcTmemSlot = 72, kTcAbort = 76;
@@ -82,7 +83,8 @@ struct TcParams {
     const uint32_t* T;
     uint64_t stride;
     uint64_t K;
-    uint64_t kslice;  // k per CTA, a multiple of kTcChunkK
+    uint64_t nchunks;  // 256-value accumulator chunks of k in all: ceil(K / 256)
+    uint32_t cpc;      // chunks per CTA: CTA x takes chunks x * cpc .. x * cpc + cpc - 1
     uint32_t* out;
     uint32_t* faults;  // the library's device fault word
     uint32_t B, W;
@@ -106,7 +108,7 @@ __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
 // Bounded wait for the phase of `bar` with the given parity.  Gives up when
 // another role of the CTA has given up (abort flag), or after kTcSpinLimit
 // polls, recording the fault and raising the flag.
-__device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
                                           uint32_t* faults) {
     for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
         if (try_wait(bar, parity)) return true;
@@ -225,10 +227,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
     char* const gbase = tc_sm + (base - raw);
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(gbase + kTcAbort);
     const uint32_t m0 = blockIdx.y * kTcM, n0 = blockIdx.z * (uint32_t)TN;
-    const uint64_t k0 = (uint64_t)blockIdx.x * p.kslice;
-    const uint64_t kend = k0 + p.kslice < p.K ? k0 + p.kslice : p.K;
-    const uint32_t nst = (uint32_t)((kend - k0 + kTcStageK - 1) / kTcStageK);
-    const uint32_t nch = (nst + kTcStagesPerChunk - 1) / kTcStagesPerChunk;
+    // this CTA's chunks of k: a run of at most cpc from cfirst; only the last
+    // chunk of all (k up to K) can be partial
+    const uint64_t cfirst = (uint64_t)blockIdx.x * p.cpc;
+    const uint32_t nch = (uint32_t)(p.nchunks - cfirst < p.cpc ? p.nchunks - cfirst : p.cpc);
+    const uint64_t klast = p.K - (cfirst + nch - 1) * kTcChunkK;
+    const uint32_t nst = (nch - 1) * kTcStagesPerChunk +
+                         (klast >= kTcChunkK ? kTcStagesPerChunk : (uint32_t)((klast + kTcStageK - 1) / kTcStageK));
+    const uint64_t kend = p.K;
+    // first k of local stage g
+    auto stage_k = [&](uint32_t g) -> uint64_t { return cfirst * kTcChunkK + (uint64_t)g * kTcStageK; };
 
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < kTcStages; ++s) {
@@ -264,20 +272,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
         const bool has_b = n4 < (uint32_t)TN / 4u;
         const uint32_t nw = n0 + 4u * n4;
         const uint32_t wval = has_b && nw < p.W ? min(4u, p.W - nw) : 0u;
-        for (uint32_t g = 0; g < nst; ++g) {
-            const uint32_t s = g & 1u;
-            const uint64_t kq = k0 + (uint64_t)g * kTcStageK + 4u * q;
+        // stage g's share words (S tile) and table words (T tile), into registers
+        auto load_a = [&](uint32_t g, uint4 (&a)[8]) {
+            const uint64_t kq = stage_k(g) + 4u * q;
             const uint32_t kval = kq < kend ? (uint32_t)(kend - kq < 4u ? kend - kq : 4u) : 0u;
-            uint4 a[8];
 #pragma unroll
             for (int it = 0; it < 8; ++it) {
                 const uint32_t m = m0 + it * 16u + cw * 2u + (lane >> 4);
                 a[it] = load4<true>(p.S + (uint64_t)m * p.ld + kq, m < p.B ? kval : 0u, p.vec);
             }
-            uint4 t[4];
+        };
+        auto load_t = [&](uint32_t g, uint4 (&t)[4]) {
+            const uint64_t kq = stage_k(g) + 4u * q;
+            const uint32_t kval = kq < kend ? (uint32_t)(kend - kq < 4u ? kend - kq : 4u) : 0u;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) t[e] = load4<false>(p.T + (kq + e) * p.stride + nw, e < (int)kval ? wval : 0u, p.vec);
-            if (!wait_bounded(base + kTcEmpty + 8u * s, ((g >> 1) & 1u) ^ 1u, abort_flag, p.faults)) break;
+            for (int e = 0; e < 4; ++e)
+                t[e] = load4<false>(p.T + (kq + e) * p.stride + nw, e < (int)kval ? wval : 0u, p.vec);
+        };
+        // stage g's words -> limb planes in shared-memory stage g % 2
+        auto convert_stage = [&](uint32_t g, const uint4 (&a)[8], const uint4 (&t)[4]) -> bool {
+            const uint32_t s = g & 1u;
+            if (!wait_bounded(base + kTcEmpty + 8u * s, ((g >> 1) & 1u) ^ 1u, abort_flag, p.faults)) return false;
             const uint32_t stage = base + kTcHeader + s * Sh::kStageBytes;
 #pragma unroll
             for (int it = 0; it < 8; ++it) {
@@ -300,6 +315,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
             // the tensor core reads the planes through the async proxy
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(base + kTcFull + 8u * s);
+            return true;
+        };
+        // registers hold the next stage's words while this one is converted;
+        // L2 holds the stages after that
+        for (uint32_t g = 0; g < nst; ++g) {
+            uint4 a[8], t[4];
+            load_a(g, a);
+            load_t(g, t);
+            if (!convert_stage(g, a, t)) break;
         }
     } else if (warp == kTcMmaWarp) {
         // ---- MMA issue: 4 k-steps x 10 limb pairs per stage ------------------
@@ -400,20 +424,21 @@ int launch_contract_tc(const uint32_t* shares, uint64_t ld, uint32_t batch, cons
     const uint32_t tn = width <= 32 ? 32u : 64u;
     const uint64_t mt = (batch + dev::kTcM - 1) / dev::kTcM, nt = (width + tn - 1) / tn;
     const uint64_t sms = (uint64_t)std::max(1, device_sm_count());
-    // one CTA per SM: the output tiles times enough k slices to fill one wave,
-    // each slice a whole number of 256-value accumulator chunks
-    uint64_t slices = std::max<uint64_t>(1, sms / (mt * nt));
-    uint64_t kslice = (rows + slices - 1) / slices;
-    kslice = (kslice + dev::kTcChunkK - 1) / dev::kTcChunkK * dev::kTcChunkK;
-    slices = (rows + kslice - 1) / kslice;
-    if (slices > 0x7fffffffull || mt > 65535 || nt > 65535) return PIR_ERR_UNSUPPORTED;
+    // one CTA per SM: the output tiles times enough CTAs along k to fill one
+    // wave, each taking whole 256-value accumulator chunks
+    const uint64_t nchunks = (rows + dev::kTcChunkK - 1) / dev::kTcChunkK;
+    uint64_t slices = std::min<uint64_t>(nchunks, std::max<uint64_t>(1, sms / (mt * nt)));
+    const uint64_t cpc = (nchunks + slices - 1) / slices;
+    slices = (nchunks + cpc - 1) / cpc;
+    if (slices > 0x7fffffffull || cpc > 0xffffffffull || mt > 65535 || nt > 65535) return PIR_ERR_UNSUPPORTED;
     dev::TcParams p;
     p.S = shares;
     p.ld = ld;
     p.T = table;
     p.stride = stride;
     p.K = rows;
-    p.kslice = kslice;
+    p.nchunks = nchunks;
+    p.cpc = (uint32_t)cpc;
     p.out = out;
     p.faults = faults;
     p.B = batch;

@@ -80,3 +80,16 @@ def test_binding_structs_match_the_header(lib, tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
+
+
+def test_binding_constants_match_the_header(lib):
+    """Every integer constant the binding re-exports under a header macro's
+    name (engines, status bits, error codes) has the header's value."""
+    defs = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define\s+(PIR_\w+)\s+\(?(-?\d+)u?\)?", open(h).read(), flags=re.M):
+            defs[m.group(1)] = int(m.group(2))
+    shared = [k for k in defs if isinstance(getattr(lib, k, None), int)]
+    assert "PIR_CONTRACT_TC_F16" in shared and "PIR_CONTRACT_IMAD" in shared
+    for k in shared:
+        assert getattr(lib, k) == defs[k], k
