@@ -451,7 +451,10 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  *    signed 8-bit limbs held exactly in fp16, the ten limb products of
  *    the low 32 bits accumulate exactly in fp32 for 256 values of k at a
  *    time and are then folded into u32 totals.  One CTA per SM (about
- *    200 KB of shared memory).  Its waits are bounded like the scan's;
+ *    200 KB of shared memory) holding its SM's tensor memory (512
+ *    columns; 256 for 32-word tiles) while it runs, so a kernel that uses
+ *    tensor memory on the same SM at the same time waits for it.  Its
+ *    waits are bounded like the scan's;
  *    one that gives up leaves dout incomplete and sets
  *    PIR_FAULT_WAIT_TIMEOUT;
  *  - PIR_CONTRACT_SCAN: for a few queries, where the product is bound by
