@@ -429,6 +429,7 @@ int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dk
 #define PIR_CONTRACT_MMA_U8 1 /* tensor-core u8 x u8 -> s32 MMAs on 8-bit limbs (10 per u32 product), exact */
 #define PIR_CONTRACT_SCAN 2   /* streaming table scan for a few queries, bound by HBM bandwidth */
 #define PIR_CONTRACT_TC_F16 3 /* tcgen05 tensor cores, fp16 signed 8-bit limbs, fp32 TMEM accumulators, exact */
+#define PIR_CONTRACT_AUTO 4   /* the engine measured fastest for the shape (see pir_contract_u32) */
 
 /* Expansion only (the level-by-level strategy's output, Sec. 3.2.2): writes
  * the full share vectors dshares[q * ld + j] = Eval(k_q, j) for j < rows,
@@ -464,7 +465,11 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  *    t->width multiples of 4 and t->stride <= 1024, else
  *    PIR_ERR_UNSUPPORTED.  Its waits on the copies are bounded: one that
  *    gives up leaves dout incomplete and sets PIR_FAULT_WAIT_TIMEOUT (see
- *    pir_device_status).
+ *    pir_device_status);
+ *  - PIR_CONTRACT_AUTO: the fastest of these as measured on GB300 for the
+ *    shape: the streaming scan for at most 24 queries where its layout
+ *    conditions hold, the tcgen05 engine otherwise (IMAD and the u8-limb
+ *    MMAs are slower than one of the two at every batch).
  * dout (device, batch x width) is overwritten.  Asynchronous. */
 int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
                      int engine, void* stream);

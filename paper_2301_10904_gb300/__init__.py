@@ -341,6 +341,7 @@ PIR_CONTRACT_IMAD = 0
 PIR_CONTRACT_MMA_U8 = 1
 PIR_CONTRACT_SCAN = 2
 PIR_CONTRACT_TC_F16 = 3
+PIR_CONTRACT_AUTO = 4
 PIR_FAULT_WAIT_TIMEOUT = 1
 
 

@@ -236,8 +236,18 @@ __global__ void __launch_bounds__(256) contract_mma_u8_kernel(const uint32_t* __
 
 }  // namespace dev
 
+// Largest batch for which PIR_CONTRACT_AUTO picks the streaming scan.  The
+// scan reads the table once per 8 queries; the tcgen05 engine converts a
+// whole 128-query tile whatever the batch.  On GB300, 2^20 x 64 words: scan
+// 0.046 / 0.059 / 0.115 / 0.229 ms at 1 / 8 / 16 / 32 queries, tcgen05
+// 0.22 ms for any batch up to 128 (IMAD 0.32-0.68 ms, never the fastest).
+constexpr uint32_t kAutoScanMaxBatch = 24;
+
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                     uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream) {
+    if (engine == PIR_CONTRACT_AUTO)  // the engine measured fastest for the shape on GB300
+        engine = batch <= kAutoScanMaxBatch && scan_supported(shares, ld, table, stride, width) ? PIR_CONTRACT_SCAN
+                                                                                                 : PIR_CONTRACT_TC_F16;
     if (engine == PIR_CONTRACT_SCAN) return launch_scan(shares, ld, batch, table, stride, width, rows, out, stream);
     if (engine == PIR_CONTRACT_TC_F16)
         return launch_contract_tc(shares, ld, batch, table, stride, width, rows, out, stream);

@@ -58,9 +58,9 @@ def test_materialised_bad_key_gives_zero_vector_and_status(env):
     assert not got[1].any() and int(status.item()) & 1
 
 
-@pytest.mark.parametrize("engine", [0, 1, 3], ids=["imad", "mma_u8", "tc_f16"])
+@pytest.mark.parametrize("engine", [0, 1, 3, 4], ids=["imad", "mma_u8", "tc_f16", "auto"])
 @pytest.mark.parametrize("B,L,W", [(1, 1, 1), (3, 100, 5), (64, 4096, 64), (70, 3000, 65), (256, 1 << 14, 16),
-                                   (5, 777, 128), (9, 20000, 32)])
+                                   (5, 777, 128), (9, 20000, 32), (6, 4096, 32), (20, 4096, 64)])
 def test_contract_matches_oracle(env, B, L, W, engine):
     torch, pir, orc = env
     rng = np.random.Generator(np.random.PCG64(B * L + W))
