@@ -147,3 +147,33 @@ def test_tc_contract_exact_at_the_accumulator_bound(env):
     S[3, :] = 0x80808080  # limbs of mixed sign in one row
     T[:, 7] = 0xFFFFFFFF
     assert np.array_equal(_tc_contract(torch, pir, S, T), orc.contract(S, T))
+
+
+@pytest.mark.parametrize("B,L,W,nrows,ncols", [(256, 1 << 20, 64, 6, 16), (1024, 1 << 24, 32, 4, 6)],
+                         ids=["batched_2^20x64", "large_2^24x32"])
+def test_tc_contract_full_size_sampled_outputs(env, B, L, W, nrows, ncols):
+    """The bench's full-size shapes, in the launch configuration the bench
+    times: seeded random shares and table on the device, the tcgen05 product,
+    and the oracle's product for a seeded sample of outputs (query rows x
+    table words, the first and last of each included)."""
+    torch, pir, orc = env
+    free = torch.cuda.mem_get_info()[0]
+    if (B + W) * L * 4 > 0.6 * free:
+        pytest.skip("not enough device memory for this shape")
+    gen = torch.Generator(device="cuda").manual_seed(B * 131 + W)
+    S = torch.randint(-2**31, 2**31 - 1, (B, L), dtype=torch.int32, device="cuda", generator=gen)
+    T = torch.randint(-2**31, 2**31 - 1, (L, W), dtype=torch.int32, device="cuda", generator=gen)
+    out = torch.empty((B, W), dtype=torch.int32, device="cuda")
+    pir.pir_contract_u32(S, B, T, out, engine=pir.PIR_CONTRACT_TC_F16)
+    torch.cuda.synchronize()
+    assert pir.pir_device_status(clear=True) == 0
+    got = out.cpu().numpy().view(np.uint32)
+    rng = np.random.Generator(np.random.PCG64(L + B))
+    rows = sorted({0, B - 1, *rng.integers(0, B, nrows - 2).tolist()})
+    cols = sorted({0, W - 1, *rng.integers(0, W, ncols - 2).tolist()})
+    Sh = S[rows].cpu().numpy().view(np.uint32)
+    Th = T[:, cols].cpu().numpy().view(np.uint32)
+    want = orc.contract(Sh, Th)
+    assert np.array_equal(got[np.ix_(rows, cols)], want)
+    del S, T
+    torch.cuda.empty_cache()
