@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
             mbar_arrive(base + kTcFull + 8u * s);
             return true;
         };
-        // registers hold the next stage's words while this one is converted;
-        // L2 holds the stages after that
+        // a stage's loads are in flight while the warp waits for a free
+        // shared-memory stage (the MMAs of two stages back)
         for (uint32_t g = 0; g < nst; ++g) {
             uint4 a[8], t[4];
             load_a(g, a);
@@ -356,8 +356,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
             }
             // every MMA issued completes before the tensor memory is freed (bounded)
             mma_commit(base + kTcDone);
-            for (uint32_t i = 0; i < kTcSpinLimit && !try_wait(base + kTcDone, 0u); ++i) {
-            }
+            bool done = false;
+            for (uint32_t i = 0; i < kTcSpinLimit && !done; ++i) done = try_wait(base + kTcDone, 0u);
+            if (!done) atomicOr(p.faults, PIR_FAULT_WAIT_TIMEOUT);
         }
         __syncwarp();
     } else {
