@@ -213,3 +213,43 @@ def test_contract_redzones(env, B, L, W, lpad, tpad, engine):
     assert np.array_equal(out.cpu().numpy().view(np.uint32), orc.contract(Sh, T))
     assert sbuf.unchanged() and tbuf.unchanged() and intact(obuf)
     assert pir.pir_device_status(clear=True) == 0
+
+
+def test_noalloc_entry_point_redzones(env):
+    """The allocation-free entry point reads a guarded, row-padded table."""
+    torch, pir, orc = env
+    rows, W, B = 3000, 16, 4
+    T = wl.table_u32(91, rows, W)
+    ks0, _ = make_keys(orc, pir.pir_domain_bits(rows), wl.alphas(92, rows, B), [1] * B, 93)
+    tbuf, table = guarded_table(torch, T, 4, 161)
+    out = np.zeros((B, W), np.uint32)
+    pir.pir_server_eval_noalloc(table, b"".join(ks0), B, out)
+    assert np.array_equal(out, _answers(orc, ks0, T))
+    assert tbuf.unchanged()
+
+
+def test_serving_redzones(env):
+    """Tables registered with a server are read, never written, and only
+    within their rows and widths, whatever the batch mix."""
+    torch, pir, orc = env
+    shapes, pads = [(2000, 16), (1 << 12, 32), (700, 8)], [4, 8, 4]
+    Ts = [wl.table_u32(170 + i, r, w) for i, (r, w) in enumerate(shapes)]
+    guarded = [guarded_table(torch, T, p, 171 + i) for i, (T, p) in enumerate(zip(Ts, pads))]
+    srv = pir.pir_server_create(max_batch=64)
+    try:
+        tids = [srv.register_table(v) for _, v in guarded]
+        rng = np.random.Generator(np.random.PCG64(172))
+        reqs = []
+        for q in range(30):
+            t = int(rng.integers(0, len(shapes)))
+            rows, W = shapes[t]
+            k0, _ = make_keys(orc, pir.pir_domain_bits(rows), [int(rng.integers(0, rows))], [1], 180 + q)
+            out = np.zeros(W, np.uint32)
+            reqs.append((t, k0[0], out, srv.submit(tids[t], k0[0], out)))
+        srv.drain()
+        for t, key, out, ticket in reqs:
+            assert srv.poll(ticket) is not None
+            assert np.array_equal(out, orc.answer(key, Ts[t]))
+    finally:
+        srv.close()
+    assert all(b.unchanged() for b, _ in guarded)
