@@ -1,5 +1,7 @@
 """The ChaCha20 PRF on the GPU (the alternative PRF of Sec. 3.2.6, Table 5):
-fused, materialised, multi-table and mixed-PRF batches against the oracle."""
+fused, materialised, multi-table and mixed-PRF batches against the oracle, and
+mixed-PRF keys through serving, range shards, the allocation-free entry point
+and the expand-and-scan strategy."""
 import numpy as np
 import pytest
 
@@ -126,3 +128,51 @@ def test_mixed_prf_every_path_and_split_shape(env):
                     assert np.array_equal(got[q], want[q]), (g, r, q)
             ran += 1
     assert ran == 24
+
+
+def test_mixed_prf_serving_shards_noalloc_and_expand_scan(env):
+    """Keys of both PRFs through the entry points not covered above: the
+    serving loop, index-range shards summed over the table, the
+    allocation-free entry point and the expand-and-scan strategy; every
+    share equals the oracle's and both parties reconstruct T[alpha]."""
+    torch, pir, orc = env
+    rows, width, batch = 5000, 16, 6
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(95, rows, width)
+    alphas = wl.alphas(95, rows, batch)
+    ks0, ks1 = _keys(orc, n, alphas, [q % 2 for q in range(batch)], 95)
+    table = dev_table(torch, T)
+    for keys in (ks0, ks1):
+        want = np.stack([orc.answer(k, T) for k in keys])
+        # expand-and-scan strategy on an explicit plan
+        plan = pir.pir_plan_for(rows, width, batch)
+        plan.strategy = pir.PIR_STRATEGY_EXPAND_SCAN
+        got = run_device(torch, pir, table, keys, width, plan=plan)
+        assert np.array_equal(got, want)
+        # index-range shards, summed mod 2^32
+        dk = dev_keys(torch, keys)
+        total = np.zeros((batch, width), np.uint64)
+        for lo, hi in ((0, 1024), (1024, 3000), (3000, rows)):
+            part = torch.empty((batch, width), dtype=torch.int32, device="cuda")
+            pir.pir_server_eval_range(table[lo:hi], lo, rows, dk, batch, part)
+            torch.cuda.synchronize()
+            total += part.cpu().numpy().view(np.uint32)
+        assert np.array_equal((total & M32).astype(np.uint32), want)
+        # allocation-free entry point
+        out = np.zeros((batch, width), np.uint32)
+        pir.pir_server_eval_noalloc(table, b"".join(keys), batch, out)
+        assert np.array_equal(out, want)
+        # serving loop
+        srv = pir.pir_server_create(max_batch=16)
+        try:
+            tid = srv.register_table(table)
+            outs = [np.zeros(width, np.uint32) for _ in keys]
+            tickets = [srv.submit(tid, k, o) for k, o in zip(keys, outs)]
+            srv.drain()
+            assert all(srv.poll(t) is not None for t in tickets)
+            assert np.array_equal(np.stack(outs), want)
+        finally:
+            srv.close()
+    rec0 = np.stack([orc.answer(k, T) for k in ks0]).astype(np.uint64)
+    rec1 = np.stack([orc.answer(k, T) for k in ks1]).astype(np.uint64)
+    assert np.array_equal(((rec0 + rec1) & M32).astype(np.uint32), T[alphas])
