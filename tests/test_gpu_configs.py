@@ -6,9 +6,13 @@
  - batched: 2^20 rows x 64 words, 256 queries: every query reconstructs
    T[alpha] exactly (both servers on the GPU), every query's server-0 share
    and a seeded sample of 16 server-1 shares match the oracle word for word;
- - large table: 2^24 rows x 32 words (2 GiB), 1024 queries: same checks with
-   two sampled queries per server (the oracle needs tens of seconds per 2^24
-   expansion; the samples run in parallel host threads).
+ - large table: 2^24 rows x 32 words (2 GiB), 1024 queries: every query
+   reconstructs T[alpha]; 16 seeded server-0 shares (queries 0 and 1023, and
+   two more whose last row range runs in the cut last round of the persistent
+   grid) and 4 server-1 shares match the oracle word for word.  Reconstruction
+   alone would not catch a dropped or misrouted row away from alpha: the two
+   servers' shares of such a row are equal and cancel.  The oracle needs tens
+   of seconds per 2^24 expansion; the samples run in parallel host threads.
 """
 import os
 
@@ -62,6 +66,7 @@ def _oracle_sample(orc, keys, T, idx):
 
 def _check_config(env, rows, width, batch, seed, sample, sample1=None):
     torch, pir, orc = env
+    q1 = sample1 if sample1 is not None else sample
     n = pir.pir_domain_bits(rows)
     table = wl.table_u32_torch(seed, rows, width, "cuda")
     alphas = wl.alphas(seed, rows, batch)
@@ -75,11 +80,11 @@ def _check_config(env, rows, width, batch, seed, sample, sample1=None):
     assert np.array_equal(rec.astype(np.uint32), rows_at)
     T = table.cpu().numpy().view(np.uint32)
     assert np.array_equal(T[[0, rows - 1]], wl.table_rows_u32(seed, width, [0, rows - 1]))
-    for q, want in zip(sample, _oracle_sample(orc, ks0, T, sample)):
-        assert np.array_equal(g0[q], want), q
-    q1 = sample1 if sample1 is not None else sample
-    for q, want in zip(q1, _oracle_sample(orc, ks1, T, q1)):
-        assert np.array_equal(g1[q], want), q
+    # both parties' samples in one pool of host threads
+    jobs = [(0, q) for q in sample] + [(1, q) for q in q1]
+    wants = _oracle_sample(orc, [(ks0, ks1)[s][q] for s, q in jobs], T, range(len(jobs)))
+    for (s, q), want in zip(jobs, wants):
+        assert np.array_equal((g0, g1)[s][q], want), (s, q)
 
 
 def test_plain_single_query_2p16x16(env):
@@ -92,8 +97,31 @@ def test_batched_2p20x64_b256(env):
     _check_config(env, 1 << 20, 64, 256, 202, list(range(256)), sample1)
 
 
+def _cut_round_queries(pir, rows, width, batch, sms):
+    """Queries whose items run in the persistent grid's cut last round: the
+    items past the last whole round of `sms` CTAs, query groups fastest."""
+    plan = pir.pir_plan_inspect(rows, width, batch, sms)
+    nqg = -(-batch // plan.group)
+    nitems = (rows >> plan.range_log2) * nqg
+    if not plan.tail_log2:
+        return []
+    first = nitems // plan.ctas * plan.ctas
+    return sorted({(it % nqg) * plan.group + g for it in range(first, nitems) for g in range(plan.group)
+                   if (it % nqg) * plan.group + g < batch})
+
+
 def test_large_2p24x32_b1024(env):
-    _check_config(env, 1 << 24, 32, 1024, 404, [1023, 0])
+    torch, pir, _ = env
+    rows, width, batch = 1 << 24, 32, 1024
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cut = _cut_round_queries(pir, rows, width, batch, sms)
+    assert len(cut) >= 3 and 1023 in cut  # the default plan on this device cuts its last round
+    rng = np.random.Generator(np.random.PCG64(404))
+    pick = [1023, 0] + [int(q) for q in rng.choice([q for q in cut if q != 1023], 2, replace=False)]
+    rest = [int(q) for q in rng.permutation(np.arange(1, 1023)) if q not in pick][:16 - len(pick)]
+    sample = pick + rest
+    assert len(set(sample)) == 16
+    _check_config(env, rows, width, batch, 404, sample, [1023, 0] + rest[:2])
 
 
 def test_single_query_on_a_large_table_two_pass_strategy(env):
