@@ -4,9 +4,12 @@
 One step = one pass of the whole server path over one batch of queries:
 key ingest from device memory, DPF full-domain expansion (AES-128 PRF) fused
 with the share x table product mod 2^32, and the reduction into the output
-shares (pir_server_eval_device).  The default workload is the batched one:
-a 2^20-row table of 64 u32 words (256 MiB, 2048-bit entries), 256 queries per
-step.  Inputs are seeded synthetic data (workloads/).
+shares (pir_server_eval_device).  The default workload is the largest
+single-GPU configuration: a 2^24-row table of 32 u32 words (2 GiB), 1024
+queries per step.  After its timed region that run also measures the other
+configurations compactly (plain single query, batched 2^20 x 64, the 8-table
+mix, the serving loop at two offered rates) under "other_configs".  Inputs are
+seeded synthetic data (workloads/).
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank drives its own GPU
 with its own queries and table copy (queries are independent: weak scaling,
@@ -20,8 +23,9 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import re
 import json
+import math
+import re
 import os
 import statistics
 import subprocess
@@ -60,6 +64,48 @@ WORKLOADS = {
                         desc="multi-table: 2048 queries Zipf(1.1) over 8 tables (2^16..2^22 rows, 16..128 words, "
                              "1,460 MiB), one graph-captured persistent launch per step"),
 }
+def workload_config(name: str, prf: int, world: int) -> dict:
+    """The `config` object of a workload's JSON line: host-side facts only, the
+    same for both arms (the product's plan and server settings are reported
+    beside it, under `plan` and `server`)."""
+    wk = WORKLOADS[name]
+    par = f"{world} replica(s), independent queries"
+    if name in ("batched_1m", "plain_64k", "large_16m"):
+        rows, width = wk["rows"], wk["width"]
+        mib = rows * width * 4 >> 20
+        return {"workload": wk["desc"], "rows": rows, "width_words": width, "batch": wk["batch"],
+                "n": wl.domain_bits(rows), "prf": PRF_NAMES[prf],
+                "l2": f"inputs larger than L2: table {mib} MiB per step, no flush" if rows * width * 4 > L2_BYTES
+                else "table fits in L2; no flush (resident-table serving)", "parallelism": par}
+    if name == "multi_table":
+        shapes = list(zip(wl.MULTI_TABLE_ROWS, wl.MULTI_TABLE_WIDTHS))
+        assign = wl.zipf_assignment(wk["seed"], len(shapes), wl.MULTI_TABLE_QUERIES)
+        return {"workload": wk["desc"], "tables": [{"rows": r, "width_words": w} for r, w in shapes],
+                "queries": wl.MULTI_TABLE_QUERIES,
+                "queries_per_table": np.bincount(assign, minlength=len(shapes)).tolist(), "prf": "AES-128",
+                "tables_mib": round(sum(r * w * 4 for r, w in shapes) / 2**20, 1),
+                "l2": "inputs larger than L2 (1,460 MiB of tables per step), no flush", "parallelism": par}
+    if name == "pbr_1m":
+        rows, width, bin_rows = wk["rows"], wk["width"], wk["bin_rows"]
+        return {"workload": wk["desc"], "rows": rows, "width_words": width, "bin_rows": bin_rows,
+                "bins": -(-rows // bin_rows), "n_per_bin": wl.domain_bits(bin_rows), "prf": PRF_NAMES[prf],
+                "l2": f"inputs larger than L2: table {rows * width * 4 >> 20} MiB per step, no flush",
+                "parallelism": par}
+    if name == "serving":
+        shapes = wl.SERVING_TABLES
+        return {"workload": wk["desc"], "tables": [{"rows": r, "width_words": w} for r, w in shapes],
+                "tables_mib": round(sum(r * w * 4 for r, w in shapes) / 2**20, 1), "prf": "AES-128",
+                "l2": "inputs larger than L2 (1,728 MiB of tables), no flush", "parallelism": par}
+    if name == "serving_hotfull":
+        full_rows, width = wl.HOTFULL_FULL
+        return {"workload": wk["desc"], "full": {"rows": full_rows, "width_words": width},
+                "hot": {"rows": wl.HOTFULL_HOT_ROWS, "width_words": width},
+                "wanted_per_request": wl.HOTFULL_WANTED, "q_hot": wl.HOTFULL_Q_HOT, "q_full": wl.HOTFULL_Q_FULL,
+                "prf": "AES-128", "l2": "inputs larger than L2 (512 MiB full table), no flush",
+                "parallelism": f"{world} replica(s), independent requests"}
+    raise KeyError(name)
+
+
 # Paper Table 4 (Sec. 5): 1M entries x 2048 bit, AES-128, one V100: 1,358 QPS (other hardware; context).
 PAPER_QPS = {"batched_1m": 1358.0}
 L2_BYTES = 129 * 1000 * 1000
@@ -84,6 +130,7 @@ def measured_hbm_gbs():
 
 
 LOOKUPS_PER_NODE = 360  # table-lookup AES-128: 40 for the key expansion + 2 x 160 for the two blocks
+ORACLE_S_PER_NODE = 1.7e-6  # the oracle's cost per tree node on one Grace core, roughly
 CHACHA_ALU_OPS_PER_NODE = 640  # ChaCha20 block: 20 rounds x 4 quarter rounds x (4 XOR + 4 rotate)
 
 
@@ -212,10 +259,25 @@ PRFS = {"aes128": 0, "chacha20": 1}
 PRF_NAMES = {0: "AES-128", 1: "ChaCha20"}
 
 
-def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float = 20.0, max_wall_s: float = 60.0,
-               prf: int = 0):
-    """Times the oracle (as it stands) on host threads: each thread evaluates whole
-    queries (FullEval + inner product).  Returns (qps, threads, queries, wall)."""
+def _oracle_jobs(rows: int, seed: int, queries: int, parts: int, prf: int):
+    """Oracle keys for `queries` seeded queries, each cut into `parts` row ranges
+    (the answer is linear over index ranges, Sec. 3.2.7: the parts' shares add up
+    to the query's share, so a range is a fair share of one query's work)."""
+    import oracle
+
+    n = wl.domain_bits(rows)
+    rnd = wl.key_randomness(seed, n, queries)
+    alphas = wl.alphas(seed, rows, queries)
+    keys = [oracle.gen(n, int(a), 1, r0, r1, c0, prf)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    cuts = [rows * i // parts for i in range(parts + 1)]
+    return [(k, cuts[i], cuts[i + 1]) for k in keys for i in range(parts)]
+
+
+def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float = 20.0, prf: int = 0):
+    """Times the oracle (as it stands) on host threads over about `target_cpu_s`
+    of CPU work: whole queries (FullEval + inner product) per thread, or, when
+    that is fewer queries than threads, each query cut into row ranges so that
+    every thread has work.  Returns (qps, threads, queries, wall)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -223,33 +285,36 @@ def oracle_qps(rows: int, width: int, seed: int, table_np, target_cpu_s: float =
     oracle.build()
     n = wl.domain_bits(rows)
     threads = os.cpu_count() or 1
-    per_query_s = 1.7e-6 * (1 << n)  # the oracle's measured cost per tree node, roughly
-    queries = max(threads, min(int(target_cpu_s / per_query_s), 64 * threads))
-    queries = max(1, min(queries, int(max_wall_s / per_query_s) * threads))
-    rnd = wl.key_randomness(seed + 1, n, queries)
-    alphas = wl.alphas(seed + 1, rows, queries)
-    keys = [oracle.gen(n, int(a), 1, r0, r1, c0, prf)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    per_query_s = ORACLE_S_PER_NODE * (1 << n)
+    queries = max(1, min(int(target_cpu_s / per_query_s + 0.5), 64 * threads))
+    parts = 1 if queries >= threads else -(-threads // queries)
+    jobs = _oracle_jobs(rows, seed + 1, queries, parts, prf)
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
-        list(ex.map(lambda k: oracle.answer(k, table_np), keys))
+        list(ex.map(lambda j: oracle.answer(j[0], table_np, j[1], j[2]), jobs))
     wall = time.perf_counter() - t0
-    return queries / wall, min(threads, queries), queries, wall
+    return queries / wall, min(threads, len(jobs)), queries, wall
 
 
 def oracle_one_core_qps(rows: int, seed: int, table_np, prf: int = 0, max_s: float = 6.0):
-    """The oracle on one host thread: queries per second over a few queries (at most ~max_s)."""
+    """The oracle on one host thread: queries per second over about max_s of
+    work (whole queries, or the first rows/parts of one query when a whole one
+    takes longer; returns the fraction of a query timed)."""
     import oracle
 
     oracle.build()
     n = wl.domain_bits(rows)
-    queries = max(1, min(8, int(max_s / (1.7e-6 * (1 << n)))))
-    rnd = wl.key_randomness(seed + 2, n, queries)
-    alphas = wl.alphas(seed + 2, rows, queries)
-    keys = [oracle.gen(n, int(a), 1, r0, r1, c0, prf)[0] for (r0, r1, c0), a in zip(rnd, alphas)]
+    per_query_s = ORACLE_S_PER_NODE * (1 << n)
+    queries = max(1, min(8, int(max_s / per_query_s)))
+    parts = max(1, 1 << max(0, math.ceil(math.log2(per_query_s / max_s)))) if queries == 1 else 1
+    jobs = _oracle_jobs(rows, seed + 2, queries, parts, prf)
+    if parts > 1:
+        jobs = jobs[:1]
     t0 = time.perf_counter()
-    for k in keys:
-        oracle.answer(k, table_np)
-    return queries / (time.perf_counter() - t0), queries
+    for k, lo, hi in jobs:
+        oracle.answer(k, table_np, lo, hi)
+    frac = (jobs[0][2] - jobs[0][1]) / rows if parts > 1 else queries
+    return frac / (time.perf_counter() - t0), frac
 
 
 def host_cpu_model() -> str:
@@ -364,12 +429,8 @@ class SingleTableWorkload:
         want = self.table[torch.from_numpy(self.alphas.astype(np.int64)).to(self.device)].cpu().numpy()
         return bool(np.array_equal((rec & 0xFFFFFFFF).astype(np.uint32), want.view(np.uint32)))
 
-    def config(self):
-        return {"workload": self.desc, "rows": self.rows, "width_words": self.width, "batch": self.batch,
-                "n": self.n, "prf": PRF_NAMES[self.prf],
-                "l2": f"inputs larger than L2: table {self.rows * self.width * 4 >> 20} MiB per step, no flush"
-                if self.rows * self.width * 4 > 129e6 else "table fits in L2; no flush (resident-table serving)",
-                "plan": self.plan.as_dict()}
+    def plan_info(self):
+        return self.plan.as_dict()
 
     def tc_roofline(self, ms, flops, s_bytes):
         """The tcgen05 contraction against both ceilings: its limb products
@@ -486,10 +547,13 @@ class SingleTableWorkload:
         table_np = self.table.cpu().numpy().view(np.uint32)
         qps, cores, nq, wall = oracle_qps(self.rows, self.width, self.seed, table_np, prf=self.prf)
         one, n1 = oracle_one_core_qps(self.rows, self.seed, table_np, prf=self.prf)
+        split = "" if nq >= cores else f", each cut into {-(-cores // nq)} row ranges over the threads"
         return {"value": round(qps, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
-                "sample": f"{nq} queries of this workload (oracle FullEval + inner product), "
+                "sample": f"{nq} queries of this workload (oracle FullEval + inner product){split}, "
                           f"{cores} host threads, {wall:.1f} s wall",
-                "one_core": {"value": round(one, 4), "sample": f"{n1} queries on one thread"},
+                "one_core": {"value": round(one, 4),
+                             "sample": f"{n1:g} queries on one thread" if n1 >= 1 else
+                             f"the first {n1:g} of one query's rows on one thread, scaled to whole queries"},
                 "nproc": os.cpu_count(), "cpu": host_cpu_model()}
 
 
@@ -550,14 +614,9 @@ class MultiTableWorkload:
                 return False
         return True
 
-    def config(self):
-        counts = np.bincount(self.assign, minlength=len(self.shapes)).tolist()
-        return {"workload": self.desc, "tables": [{"rows": r, "width_words": w} for r, w in self.shapes],
-                "queries": self.batch, "queries_per_table": counts, "prf": "AES-128",
-                "tables_mib": round(sum(r * w * 4 for r, w in self.shapes) / 2**20, 1),
-                "l2": "inputs larger than L2 (1,460 MiB of tables per step), no flush",
-                "plan": {"item_log2": self.item_log2, "items": self.plan.items, "autotune_ms": round(self.tune_ms, 3),
-                         "graph": True}}
+    def plan_info(self):
+        return {"item_log2": self.item_log2, "items": self.plan.items, "autotune_ms": round(self.tune_ms, 3),
+                "graph": True}
 
     def extras(self):
         # one launch per table (pir_server_eval_device on each table's queries), back to back
@@ -605,6 +664,81 @@ class MultiTableWorkload:
                                             f"inner product), {min(threads, len(sample))} host threads, {wall:.1f} s wall"}
 
 
+class ServingMix:
+    """The serving loop over the 4 resident tables of the serving workload, with
+    seeded requests (table uniform, alpha uniform) and both parties' keys."""
+
+    def __init__(self, pir, torch, device, seed, max_count):
+        self.pir, self.torch, self.device, self.seed = pir, torch, device, seed
+        self.shapes = shapes = wl.SERVING_TABLES
+        self.tables = [wl.table_u32_torch(seed * 100 + i, r, w, device) for i, (r, w) in enumerate(shapes)]
+        ns = [pir.pir_domain_bits(r) for r, _ in shapes]
+        self.srv = pir.Server(max_batch=2048, streams=2)
+        self.tids = [self.srv.register_table(t) for t in self.tables]
+        self.assign = wl.uniform_tables(seed, len(shapes), max_count)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.alphas = [int(rng.integers(0, shapes[t][0])) for t in self.assign]
+        self.pairs = [pir.pir_keygen(ns[t], a, 1, hashlib.sha256(b"serve%d-%d" % (seed, q)).digest())
+                      for q, (t, a) in enumerate(zip(self.assign, self.alphas))]
+        self.widths = np.array([shapes[t][1] for t in self.assign], np.uint64)
+        self.out_off = np.concatenate([[0], np.cumsum(self.widths)[:-1]]).astype(np.uint64)
+        self.klens = np.array([len(p[0]) for p in self.pairs], np.uint64)
+        self.key_off = np.concatenate([[0], np.cumsum(self.klens)[:-1]]).astype(np.uint64)
+        self.keys = (b"".join(p[0] for p in self.pairs), b"".join(p[1] for p in self.pairs))
+        self.outs = np.zeros(int(self.widths.sum()), np.uint32)
+
+    def replay(self, rate, count, party=0, outs=None):
+        """Poisson arrivals at `rate` queries/s for the first `count` requests:
+        per-request latencies (ns) and the elapsed time (s)."""
+        arr = wl.poisson_arrivals(self.seed + rate, rate, count)
+        return self.srv.replay(arr, [self.tids[t] for t in self.assign[:count]], self.keys[party],
+                               self.key_off[:count], self.outs if outs is None else outs, self.out_off[:count])
+
+    def check(self, nchk):
+        """Both servers over the first requests reconstruct their rows."""
+        outs0, outs1 = np.zeros_like(self.outs), np.zeros_like(self.outs)
+        self.replay(2000, nchk, 0, outs0)
+        self.replay(2000, nchk, 1, outs1)
+        ok = True
+        for q in range(nchk):
+            o, w = int(self.out_off[q]), int(self.widths[q])
+            rec = ((outs0[o:o + w].astype(np.uint64) + outs1[o:o + w]) & 0xFFFFFFFF).astype(np.uint32)
+            ok = ok and np.array_equal(rec, self.tables[self.assign[q]][self.alphas[q]].cpu().numpy().view(np.uint32))
+        return ok
+
+    def rate_result(self, rate, count):
+        lat, el = self.replay(rate, count)
+        lat_ms = lat / 1e6
+        return {"offered_qps": rate, "requests": count, "achieved_qps": round(count / el, 1),
+                "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)}
+
+    def plain(self, nq=64):
+        """Each query alone in its own launch (pir_server_eval_device), same table mix."""
+        torch, pir, device = self.torch, self.pir, self.device
+        dk = [torch.frombuffer(bytearray(self.pairs[q][0]), dtype=torch.uint8).to(device) for q in range(nq)]
+        po = [torch.empty((1, self.shapes[self.assign[q]][1]), dtype=torch.int32, device=device) for q in range(nq)]
+        stream = torch.cuda.current_stream(device)
+        for q in range(4):
+            pir.pir_server_eval_device(self.tables[self.assign[q]], dk[q], 1, po[q], stream=stream)
+        torch.cuda.synchronize(device)
+        plain = []
+        for q in range(nq):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pir.pir_server_eval_device(self.tables[self.assign[q]], dk[q], 1, po[q], stream=stream)
+            b.record(stream)
+            b.synchronize()
+            plain.append(a.elapsed_time(b))
+        return {"qps": round(1e3 / statistics.mean(plain), 2), "p50_ms": round(float(np.percentile(plain, 50)), 4),
+                "p99_ms": round(float(np.percentile(plain, 99)), 4), "launches": len(plain)}
+
+    def close(self):
+        st = self.srv.stats()
+        self.srv.close()
+        return st
+
+
 def run_serving(args):
     """Open-loop Poisson load on the serving loop over 4 resident tables."""
     import torch
@@ -620,72 +754,20 @@ def run_serving(args):
 
     wk = WORKLOADS["serving"]
     seed = rank_seed(wk["seed"], rank)
-    shapes = wl.SERVING_TABLES
-    tables = [wl.table_u32_torch(seed * 100 + i, r, w, device) for i, (r, w) in enumerate(shapes)]
-    ns = [pir.pir_domain_bits(r) for r, _ in shapes]
-    srv = pir.Server(max_batch=2048, streams=2)
-    tids = [srv.register_table(t) for t in tables]
     rates = [int(x) for x in args.rates.split(",")]
     max_count = max(min(int(r * args.seconds), args.max_requests) for r in rates)
-    assign = wl.uniform_tables(seed, len(shapes), max_count)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    alphas = [int(rng.integers(0, shapes[t][0])) for t in assign]
-    pairs = [pir.pir_keygen(ns[t], a, 1, hashlib.sha256(b"serve%d-%d" % (seed, q)).digest())
-             for q, (t, a) in enumerate(zip(assign, alphas))]
-    widths = np.array([shapes[t][1] for t in assign], np.uint64)
-    out_off = np.concatenate([[0], np.cumsum(widths)[:-1]]).astype(np.uint64)
-    klens = np.array([len(p[0]) for p in pairs], np.uint64)
-    key_off = np.concatenate([[0], np.cumsum(klens)[:-1]]).astype(np.uint64)
-    keys0 = b"".join(p[0] for p in pairs)
-    keys1 = b"".join(p[1] for p in pairs)
-
-    def replay(rate, count, keys, outs):
-        arr = wl.poisson_arrivals(seed + rate, rate, count)
-        lat, el = srv.replay(arr, [tids[t] for t in assign[:count]], keys, key_off[:count], outs, out_off[:count])
-        return lat, el
-
-    # warm-up (builds lookup tables, allocates the batch buffers)
-    outs0 = np.zeros(int(widths.sum()), np.uint32)
-    replay(1000, min(200, max_count), keys0, outs0)
-    # correctness: both servers over the first requests reconstruct their rows
-    nchk = min(512, max_count)
-    outs1 = np.zeros(int(widths.sum()), np.uint32)
-    replay(2000, nchk, keys0, outs0)
-    replay(2000, nchk, keys1, outs1)
-    ok = True
-    for q in range(nchk):
-        o, w = int(out_off[q]), int(widths[q])
-        rec = ((outs0[o:o + w].astype(np.uint64) + outs1[o:o + w]) & 0xFFFFFFFF).astype(np.uint32)
-        ok = ok and np.array_equal(rec, tables[assign[q]][alphas[q]].cpu().numpy().view(np.uint32))
+    mix = ServingMix(pir, torch, device, seed, max_count)
+    mix.replay(1000, min(200, max_count))  # warm-up (builds lookup tables, allocates the batch buffers)
+    ok = mix.check(min(512, max_count))
 
     results = []
     sampler = ClockSampler(gpu_id_for(device) if rank == 0 else None)
     barrier(world, device)
     with sampler if rank == 0 else _Null():
         for rate in rates:
-            count = min(int(rate * args.seconds), args.max_requests)
-            lat, el = replay(rate, count, keys0, outs0)
-            lat_ms = lat / 1e6
-            results.append({"offered_qps": rate, "requests": count, "achieved_qps": round(count / el, 1),
-                            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
-                            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)})
-    st = srv.stats()
-    # plain path: each query alone in its own launch, same table mix
-    dk = [torch.frombuffer(bytearray(pairs[q][0]), dtype=torch.uint8).to(device) for q in range(64)]
-    po = [torch.empty((1, shapes[assign[q]][1]), dtype=torch.int32, device=device) for q in range(64)]
-    stream = torch.cuda.current_stream(device)
-    for q in range(4):
-        pir.pir_server_eval_device(tables[assign[q]], dk[q], 1, po[q], stream=stream)
-    torch.cuda.synchronize(device)
-    plain = []
-    for q in range(64):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pir.pir_server_eval_device(tables[assign[q]], dk[q], 1, po[q], stream=stream)
-        b.record(stream)
-        b.synchronize()
-        plain.append(a.elapsed_time(b))
-    srv.close()
+            results.append(mix.rate_result(rate, min(int(rate * args.seconds), args.max_requests)))
+    plain = mix.plain()
+    st = mix.close()
     if rank != 0:
         return
     best = max(results, key=lambda r: r["achieved_qps"])
@@ -697,21 +779,17 @@ def run_serving(args):
         "steps": total_req, "warmup": 200, "ms_per_step": round(1e3 / best["achieved_qps"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64 tables, uniform alpha and table, Poisson arrivals, keys from pir_keygen)",
-        "config": {"workload": wk["desc"], "tables": [{"rows": r, "width_words": w} for r, w in shapes],
-                   "tables_mib": round(sum(r * w * 4 for r, w in shapes) / 2**20, 1), "prf": "AES-128",
-                   "server": {"max_batch": 2048, "streams": 2, "max_inflight": st["max_inflight"]},
-                   "l2": "inputs larger than L2 (1,728 MiB of tables), no flush",
-                   "parallelism": f"{world} replica(s), independent queries"},
+        "config": workload_config("serving", 0, world),
+        "server": {"max_batch": 2048, "streams": 2, "max_inflight": st["max_inflight"]},
         "latency_ms": {"p50": knee["p50_ms"], "p99": knee["p99_ms"], "at_offered_qps": knee["offered_qps"]},
         "rates": results,
         "saturation": {"achieved_qps": best["achieved_qps"], "offered_qps": best["offered_qps"],
                        "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"]},
         "knee_offered_qps": knee["offered_qps"],
-        "plain": {"qps": round(1e3 / statistics.mean(plain), 2), "p50_ms": round(float(np.percentile(plain, 50)), 4),
-                  "p99_ms": round(float(np.percentile(plain, 99)), 4), "launches": len(plain)},
+        "plain": plain,
         "gpu_launches": st["batches"], "server_stats": st,
         "e2e": {"value": best["achieved_qps"], "unit": "queries/s",
-                "h2d_bytes_per_step": int(klens.mean()), "d2h_bytes_per_step": int(widths.mean() * 4),
+                "h2d_bytes_per_step": int(mix.klens.mean()), "d2h_bytes_per_step": int(mix.widths.mean() * 4),
                 "note": "the serving loop is end to end: host keys in, host shares out; per query"},
         "selfcheck_reconstruct_all": ok, "clocks": sampler.summary(),
     }
@@ -823,12 +901,8 @@ def run_serving_hotfull(args):
         "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded SplitMix64 table, Zipf(1.1) row popularity through a seeded permutation, "
                 "Poisson request arrivals, keys from pir_hotfull_keygen)",
-        "config": {"workload": wk["desc"], "full": {"rows": full_rows, "width_words": width},
-                   "hot": {"rows": int(hot_rows.size), "width_words": width}, "wanted_per_request": K,
-                   "q_hot": qh, "q_full": qf, "prf": "AES-128",
-                   "server": {"max_batch": 2048, "streams": 2, "max_inflight": st["max_inflight"]},
-                   "l2": "inputs larger than L2 (512 MiB full table), no flush",
-                   "parallelism": f"{world} replica(s), independent requests"},
+        "config": workload_config("serving_hotfull", 0, world),
+        "server": {"max_batch": 2048, "streams": 2, "max_inflight": st["max_inflight"]},
         "latency_ms": {"p50": knee["p50_ms"], "p99": knee["p99_ms"], "at_offered_rps": knee["offered_rps"]},
         "requests_per_s": best["achieved_rps"],
         "rates": results[True],
@@ -926,11 +1000,6 @@ class PbrWorkload:
         claimed[idx // self.bin_rows] = True
         return bool(np.array_equal(rec[idx // self.bin_rows], want) and not rec[~claimed].any())
 
-    def config(self):
-        return {"workload": self.desc, "rows": self.rows, "width_words": self.width, "bin_rows": self.bin_rows,
-                "bins": self.nbins, "n_per_bin": self.nb, "prf": PRF_NAMES[self.prf],
-                "l2": f"inputs larger than L2: table {self.rows * self.width * 4 >> 20} MiB per step, no flush"}
-
     def extras(self):
         return {"pbr": {"wanted_rows_per_step": int(len(self.wanted)), "retrieved_rows_per_step": int(self.kept.sum()),
                         "dropped_fraction": round(1.0 - float(self.kept.sum()) / len(self.wanted), 4),
@@ -1023,6 +1092,8 @@ def run_ours(args):
     e2e_total = max_over_ranks(sum(e2e_ms), world, device)
     e2e_ok = W.e2e_matches()
     extras = W.extras()
+    if world == 1 and args.other_configs and args.workload == "large_16m":
+        extras["other_configs"] = other_configs(args, pir, torch, device, stream)
 
     if rank != 0:
         return
@@ -1045,8 +1116,7 @@ def run_ours(args):
         work = f"{LOOKUPS_PER_NODE} AES table lookups x {W.nodes_per_step} tree nodes per launch"
         basis = f"{sms} SMs x 32 shared-memory lookups/clk x {max_mhz:.0f} MHz (derived)"
     achieved = per_node * W.nodes_per_step / (kernel_ms / 1e3) / 1e9
-    cfg = W.config()
-    cfg["parallelism"] = f"{world} replica(s), independent queries"
+    cfg = workload_config(args.workload, getattr(W, "prf", 0), world)
     out = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -1063,6 +1133,7 @@ def run_ours(args):
         "dtype": "u32",
         "data": "synthetic (seeded SplitMix64 tables, uniform alpha, keys from pir_keygen)",
         "config": cfg,
+        **({"plan": W.plan_info()} if hasattr(W, "plan_info") else {}),
         "latency_ms": {"p50": round(float(np.percentile(per_step, 50)), 4),
                        "p99": round(float(np.percentile(per_step, 99)), 4)},
         "gpu_launches": steps * getattr(W, "launches_per_step", 1),
@@ -1081,6 +1152,77 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = W.cpu_baseline()
     print(json.dumps(out), flush=True)
+
+
+def _events_ms(torch, stream, fn, reps):
+    """Total device time of `reps` back-to-back calls, CUDA events on the launching stream."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def other_configs(args, pir, torch, device, stream):
+    """Compact measurements of the four other workload configurations, run in
+    the headline run's process after its timed region: the plain single query
+    (2^16 x 16), the batched table (2^20 x 64, 256 queries), the 8-table Zipf
+    mix (graph replay) and the serving loop at one offered rate below its knee
+    and one above.  Each reports its own bit-exact reconstruction check."""
+    out = {}
+    wk = WORKLOADS["plain_64k"]
+    P = SingleTableWorkload("plain_64k", wk, pir, torch, device, stream, wk["seed"], args)
+    for _ in range(10):
+        P.step()
+    torch.cuda.synchronize(device)
+    lat = []
+    for _ in range(100):
+        lat.append(_events_ms(torch, stream, P.step, 1))
+    back = _events_ms(torch, stream, P.step, 200) / 200
+    for _ in range(5):
+        P.e2e_step()
+    e2e = _events_ms(torch, stream, P.e2e_step, 200) / 200
+    out["plain_64k"] = {"workload": wk["desc"], "device_us_per_query": round(back * 1e3, 2),
+                        "qps": round(1e3 / back, 1), "p50_us": round(float(np.percentile(lat, 50)) * 1e3, 2),
+                        "p99_us": round(float(np.percentile(lat, 99)) * 1e3, 2),
+                        "e2e_qps": round(1e3 / e2e, 1), "e2e_us_per_query": round(e2e * 1e3, 2),
+                        "e2e_note": "pir_server_eval: pinned host key in, pinned host share out, one call per query",
+                        "plan": P.plan_info(), "selfcheck_reconstruct_all": P.selfcheck(),
+                        "e2e_bit_exact_vs_device": P.e2e_matches()}
+    del P
+    wk = WORKLOADS["batched_1m"]
+    B = SingleTableWorkload("batched_1m", wk, pir, torch, device, stream, wk["seed"], args)
+    for _ in range(3):
+        B.step()
+    ms = _events_ms(torch, stream, B.step, 10) / 10
+    qps = B.batch / (ms / 1e3)
+    out["batched_1m"] = {"workload": wk["desc"], "qps": round(qps, 1), "ms_per_step": round(ms, 4),
+                         "vs_paper_table4": round(qps / PAPER_QPS["batched_1m"], 2),
+                         "plan": B.plan_info(), "selfcheck_reconstruct_all": B.selfcheck()}
+    del B
+    wk = WORKLOADS["multi_table"]
+    M = MultiTableWorkload("multi_table", wk, pir, torch, device, stream, wk["seed"], args)
+    for _ in range(3):
+        M.step()
+    ms = _events_ms(torch, stream, M.step, 10) / 10
+    out["multi_table"] = {"workload": wk["desc"], "qps": round(M.batch / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+                          "plan": M.plan_info(), "selfcheck_reconstruct_all": M.selfcheck()}
+    del M
+    wk = WORKLOADS["serving"]
+    rates = (2000, 8000)
+    mix = ServingMix(pir, torch, device, wk["seed"], 4000)
+    mix.replay(1000, 200)
+    ok = mix.check(256)
+    res = [mix.rate_result(2000, 2000), mix.rate_result(8000, 4000)]
+    plain = mix.plain(32)
+    st = mix.close()
+    out["serving"] = {"workload": wk["desc"], "rates": res, "plain": plain, "batches": st["batches"],
+                      "note": f"offered {rates[0]} queries/s is below the saturation knee, {rates[1]} above it",
+                      "selfcheck_reconstruct_all": ok}
+    torch.cuda.synchronize(device)
+    return out
 
 
 class _Null:
@@ -1186,8 +1328,7 @@ def run_reference(args):
         table_np = wl.table_u32(wk["seed"], rows, width)
 
         def one_step(i, quick=False):
-            return oracle_qps(rows, width, wk["seed"], table_np, target_cpu_s=2.0 if quick else 4.0,
-                              max_wall_s=8.0 if quick else 12.0)
+            return oracle_qps(rows, width, wk["seed"] + i, table_np, target_cpu_s=2.0 if quick else 4.0)
     for i in range(warm):
         one_step(i)
     times, queries, cores = [], 0, 1
@@ -1202,9 +1343,10 @@ def run_reference(args):
         "metric": METRIC, "value": round(value, 4), "unit": "queries/s", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": round(1e3 * total / steps, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": wk["desc"], "rows": rows, "width_words": width},
+        "config": workload_config(args.workload, 0, world),
         "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{queries // steps} queries per step (oracle FullEval + inner product), "
+                         "sample": f"{queries // steps} queries per step (oracle FullEval + inner product; "
+                                   f"a query longer than the step is cut into row ranges over the threads), "
                                    f"{cores} host threads"},
         "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1217,7 +1359,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched_1m")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_16m")
     ap.add_argument("--prf", choices=sorted(PRFS), default="aes128",
                     help="PRF of the keys (single-table workloads): AES-128 or ChaCha20 (Sec. 3.2.6, Table 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1229,6 +1371,8 @@ def main(argv=None):
     ap.add_argument("--max-requests", type=int, default=8000, help="serving workload: requests per rate, at most")
     ap.add_argument("--no-materialised", dest="materialised", action="store_false",
                     help="skip the materialised (share matrix in HBM) comparison leg")
+    ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
+                    help="large_16m at N=1: skip the compact runs of the other four configurations")
     ap.add_argument("--no-scan", dest="scan", action="store_false",
                     help="skip the streaming-scan (HBM roofline) leg on tables larger than L2")
     args = ap.parse_args(argv)
