@@ -86,10 +86,18 @@ typedef struct pir_table {
 
 /* How a single-table evaluation runs: the fused kernel (expansion and product
  * in one launch, Sec. 3.2.4), or expansion into stream-ordered scratch followed
- * by the streaming table scan (Sec. 3.2.2's level-by-level strategy; the
- * faster one on GB300 for a lone query on a large table). */
+ * by the streaming table scan (Sec. 3.2.2's level-by-level strategy), or the
+ * fused kernel with its table scan staged through shared memory: one more warp
+ * has the bulk-copy engine move each hand-off's table rows into a ring of
+ * shared-memory stages ahead of the consumers, so that a group of one to four
+ * queries keeps enough of the table in flight (the share vector still never
+ * leaves the SM).  PIR_STRATEGY_FUSED_STAGED needs 16-byte rows (vec 4), group
+ * <= 4, stride <= 256 words and subtrees shallow enough to leave at least two
+ * DFS stack levels free for the ring (range_log2 - min(log2(512/group),
+ * range_log2 - 1) <= 7); otherwise PIR_ERR_UNSUPPORTED. */
 #define PIR_STRATEGY_FUSED 0u
 #define PIR_STRATEGY_EXPAND_SCAN 1u
+#define PIR_STRATEGY_FUSED_STAGED 2u
 
 /* Launch shape of the fused kernel.  `group` queries share one CTA and one
  * pass over each table tile; each work item covers 2^range_log2 consecutive
@@ -105,7 +113,7 @@ typedef struct pir_plan {
     uint32_t range_log2; /* log2 rows per work item, 1 <= range_log2 <= n */
     uint32_t vec;        /* table words per load: 4 (128-bit) or 1 */
     uint32_t ctas;       /* resulting grid size (output of pir_plan_for) */
-    uint32_t strategy;   /* PIR_STRATEGY_FUSED or PIR_STRATEGY_EXPAND_SCAN */
+    uint32_t strategy;   /* PIR_STRATEGY_FUSED, _EXPAND_SCAN or _FUSED_STAGED */
     uint32_t tail_log2;  /* 0..min(3, range_log2 - 1): pieces per item of a partial last round */
 } pir_plan;
 
@@ -208,11 +216,13 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
  * dstatus: optional device word; PIR_STATUS_BAD_KEY is OR-ed into it when a
  * key fails validation on the device, and that query's share is 0.
  * Strategy: the autotuned one for this shape (pir_autotune), else the fused
- * kernel, except for a single query against a table of 256 MiB or more with
- * 16-byte rows (stride <= 1024), which is expanded into stream-ordered
- * scratch of batch x rows x 4 bytes from the library's pool and contracted by
- * the streaming scan (PIR_STRATEGY_EXPAND_SCAN; faster there on GB300).  Same
- * result bit for bit.  Asynchronous on `stream`. */
+ * kernel, except for one or two queries against a table of 128 MiB or more
+ * whose rows hold at least 64 words per query, with 16-byte rows (stride <=
+ * 1024): those are expanded into stream-ordered scratch of batch x rows x 4
+ * bytes from the library's pool and contracted by the streaming scan
+ * (PIR_STRATEGY_EXPAND_SCAN; faster there on GB300, where each table row read
+ * serves too few queries for the fused kernel's product side).  Same result
+ * bit for bit.  Asynchronous on `stream`. */
 int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                            uint32_t* dstatus, void* stream);
 
@@ -335,7 +345,7 @@ int pir_multi_autotune(const pir_table* tables, size_t ntables, const uint32_t* 
 
 /* A server with resident tables that batches queries as they arrive
  * (continuous cross-table batching).  The paper tunes a batch size per table
- * offline (Sec. 3.2.1, Sec. 5 "batch size is tuned for each experiment");
+ * offline (Sec. 3.2.1; Sec. 5 tunes it per experiment);
  * here the batch is whatever arrived while the previous batch ran.
  * Requests are admitted into max_inflight slots (from a device-memory
  * budget); a full pool refuses with PIR_ERR_BUSY.  A worker thread packs
@@ -442,8 +452,8 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
                            uint32_t* dstatus, void* stream);
 
 /* dout[q][w] = sum_{j < t->rows} dshares[q * ld + j] * T[j][w]  (mod 2^32),
- * the share-matrix x table product of Sec. 3.1 ("batched together as a
- * single matrix-matrix multiplication").  engine (same result bit for bit):
+ * the share-matrix x table product of Sec. 3.1 (a batch of queries as one
+ * matrix-matrix product).  engine (same result bit for bit):
  *  - PIR_CONTRACT_IMAD: 64 x 64 output tiles on CUDA cores, any batch;
  *  - PIR_CONTRACT_MMA_U8: the same tiles on the tensor pipe (8-bit limbs);
  *  - PIR_CONTRACT_TC_F16: 128-query x 64-word tiles (32 words when
@@ -488,8 +498,10 @@ int pir_plan_inspect(uint64_t rows, uint32_t width, size_t batch, uint32_t sms, 
  * batch and strategy per table size, Sec. 3.2.1 and 3.2.5): times, on this
  * table and batch (device keys dkeys, device shares dout; synchronizes
  * `stream`), the fused kernel for query groups G in {8,4,2,1} and rows per
- * item 2^r around the heuristic's choice, and, where the layout allows it and
- * batch <= 8, the expand-and-scan strategy; remembers the fastest for
+ * item 2^r around the heuristic's choice, the staged fused kernel
+ * (PIR_STRATEGY_FUSED_STAGED) for G <= 4 at the heuristic's rows per item and
+ * half of it, and, where the layout allows it and batch <= 8, the
+ * expand-and-scan strategy; remembers the fastest for
  * (device, rows, width, batch rounded up to a power of two).
  * pir_server_eval, pir_server_eval_device and pir_plan_for use it from then
  * on (pir_server_eval_noalloc always runs the fused kernel on its own plan).  Returns it in *plan and its time per launch in

@@ -12,7 +12,7 @@
  *     (Cipher), Sec. 5.2 (KeyExpansion).  The S-box is derived from its
  *     definition (multiplicative inverse, then the affine map), not typed in.
  *   - PRF_s(x) = AES-128 under key s of the block (x, 0, ..., 0) (Sec. 3.1,
- *     text under Eq. p3: "encrypts a message x with an encryption key s").
+ *     text under Eq. p3: the PRF is a cipher keyed by s applied to x).
  *     Alternative PRF (Sec. 3.2.6, Table 5): ChaCha20 (RFC 8439 Sec. 2.1-2.3),
  *     block 0 under key s || 0^128 and an all-zero nonce, PRF_s(x) = its 16
  *     bytes at offset 16x.  The key header names the PRF.

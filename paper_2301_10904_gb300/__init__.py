@@ -55,6 +55,7 @@ class pir_server_stats(ctypes.Structure):
 
 PIR_STRATEGY_FUSED = 0
 PIR_STRATEGY_EXPAND_SCAN = 1
+PIR_STRATEGY_FUSED_STAGED = 2
 
 
 class pir_work_item(ctypes.Structure):

@@ -114,14 +114,23 @@ static bool tuned_plan(uint64_t rows, uint32_t width, size_t batch, bool vec, pi
 
 // Runs the fused evaluation of rows [row_lo, row_lo + shard->rows) of a
 // 2^n-leaf domain for device keys into a zeroed device output.
-// One query against a table of at least kTwoPassMinBytes: expanding its share
-// vector into scratch (the level-by-level strategy, Sec. 3.2.2) and streaming the
-// table once through the scan engine beats the fused kernel, whose product side
-// cannot keep enough loads in flight for a single query (GB300: 136 vs 177 us at
-// 2^20 x 64 words, 1.10 vs 1.29 ms at 2^24 x 32; from two queries on the fused
-// kernel is as fast or faster).  The scratch (rows x 4 bytes) comes from the
-// staging pool.
-constexpr uint64_t kTwoPassMinBytes = 256ull << 20;
+// One or two queries against a table whose rows are wide for the batch (at
+// least kTwoPassRowWords words per query) and of at least kTwoPassMinBytes:
+// expanding the share vectors into scratch (the level-by-level strategy, Sec.
+// 3.2.2) and streaming the table once through the scan engine beats the fused
+// kernel.  There each table row read serves one or two queries, and the fused
+// consumers' loads queue behind the producers' table lookups in the SM's
+// shared-memory pipe, so too few rows are in flight.  GB300, one query: 2^20 x
+// 64 words 0.107 vs 0.130 ms, 2^22 x 64 0.366 vs 0.441, 2^24 x 64 1.33 vs 1.57,
+// 2^19 x 128 0.086 vs 0.102; two queries, 2^20 x 128 0.200 vs 0.227.  With
+// narrower rows the fused kernel wins: one query on 2^24 x 32 0.966 vs 1.028
+// ms, 2^22 x 32 0.279 vs 0.292; two on 2^20 x 64 0.151 vs 0.159.  The scratch
+// (rows x 4 bytes per query) comes from the staging pool.
+constexpr uint64_t kTwoPassMinBytes = 128ull << 20;
+constexpr uint32_t kTwoPassRowWords = 64;
+static bool two_pass_preferred(uint64_t rows, uint32_t width, size_t batch) {
+    return batch <= 2 && width >= kTwoPassRowWords * batch && rows * (uint64_t)width * 4u >= kTwoPassMinBytes;
+}
 
 static int eval_two_pass(const pir_table* t, uint32_t n, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                          uint32_t* dstatus, void* stream) {
@@ -172,8 +181,11 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
             if (!two_ok) return PIR_ERR_UNSUPPORTED;
             return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
         }
-        if (plan.strategy != PIR_STRATEGY_FUSED) return PIR_ERR_ARG;
-        int rc = plan_check(plan, n, shard->width, v);
+        int rc = PIR_ERR_ARG;
+        if (plan.strategy == PIR_STRATEGY_FUSED)
+            rc = plan_check(plan, n, shard->width, v);
+        else if (plan.strategy == PIR_STRATEGY_FUSED_STAGED)
+            rc = plan_check_staged(plan, n, shard->width, shard->stride, v);
         if (rc != PIR_OK) return rc;
         have = true;
     } else if (row_lo == 0 && tuned_plan(shard->rows, shard->width, batch, v, &plan)) {
@@ -181,10 +193,12 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
             return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
         // tuned per power-of-two batch bucket: cut the last round for this batch
         plan.tail_log2 = plan_tail_log2(0, shard->rows, n, plan.group, (uint32_t)batch, plan.range_log2);
-        have = plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK;
+        have = (plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK) ||
+               (plan.strategy == PIR_STRATEGY_FUSED_STAGED &&
+                plan_check_staged(plan, n, shard->width, shard->stride, v) == PIR_OK);
     }
     if (!have) {
-        if (two_ok && batch == 1 && (uint64_t)shard->rows * shard->width * 4u >= kTwoPassMinBytes)
+        if (two_ok && two_pass_preferred(shard->rows, shard->width, batch))
             return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
         int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
         if (rc != PIR_OK) return rc;
@@ -234,8 +248,7 @@ static int heuristic_plan(uint64_t rows, uint32_t width, size_t batch, int sms, 
     const uint32_t n = pir_domain_bits(rows);
     if (n == 0) return PIR_ERR_DOMAIN;
     const int rc = pir::plan_fused_sms(rows, 0, n, width, (uint32_t)batch, width % 4 == 0, sms, plan);
-    if (rc == PIR_OK && batch == 1 && width % 4 == 0 && width <= 1024 &&
-        rows * (uint64_t)width * 4u >= pir::kTwoPassMinBytes)
+    if (rc == PIR_OK && width % 4 == 0 && width <= 1024 && pir::two_pass_preferred(rows, width, batch))
         plan->strategy = PIR_STRATEGY_EXPAND_SCAN;
     return rc;
 }
@@ -280,24 +293,35 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
             const uint64_t items = (((t->rows - 1) >> r) + 1) * nqg;
             if (items < (uint64_t)std::max(1, device_sm_count()) / 2 && r != (int)n && r > 8) continue;
             if (r + 6 < (int)base.range_log2) break;  // far below the heuristic: only more path walks
-            rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);  // warm-up
-            if (rc != PIR_OK) break;
-            cudaEventRecord(a, s);
-            for (int i = 0; i < 3 && rc == PIR_OK; ++i) rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);
-            cudaEventRecord(b, s);
-            cudaError_t e = cudaEventSynchronize(b);
-            if (rc != PIR_OK) break;
-            if (e != cudaSuccess) {
-                rc = cuda_fail((int)e, "autotune sync");
-                break;
+            // the fused kernel, and for small groups near the heuristic's rows per item
+            // also its staged form (table rows through the shared-memory ring)
+            for (uint32_t strat : {PIR_STRATEGY_FUSED, PIR_STRATEGY_FUSED_STAGED}) {
+                pl.strategy = strat;
+                if (strat == PIR_STRATEGY_FUSED_STAGED &&
+                    (g > 4 || r + 1 < (int)base.range_log2 || r > (int)base.range_log2 ||
+                     plan_check_staged(pl, n, t->width, t->stride, v) != PIR_OK))
+                    continue;
+                rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);  // warm-up
+                if (rc != PIR_OK) break;
+                cudaEventRecord(a, s);
+                for (int i = 0; i < 3 && rc == PIR_OK; ++i)
+                    rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, &pl, stream);
+                cudaEventRecord(b, s);
+                cudaError_t e = cudaEventSynchronize(b);
+                if (rc != PIR_OK) break;
+                if (e != cudaSuccess) {
+                    rc = cuda_fail((int)e, "autotune sync");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                ms /= 3.f;
+                if (best_t < 0.f || ms < best_t) {
+                    best_t = ms;
+                    best = pl;
+                }
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            ms /= 3.f;
-            if (best_t < 0.f || ms < best_t) {
-                best_t = ms;
-                best = pl;
-            }
+            if (rc != PIR_OK) break;
         }
         if (rc != PIR_OK) break;
         if (g == 1) break;

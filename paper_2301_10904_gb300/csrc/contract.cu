@@ -1,7 +1,6 @@
 // Share matrix x table mod 2^32 on CUDA cores: the unfused second half of the
 // level-by-level baseline (paper Sec. 3.2.2 / 3.2.4: DPF output B x L times the
-// table L x W, "batched together as a single matrix-matrix multiplication",
-// Sec. 3.1).
+// table L x W as one matrix-matrix product, Sec. 3.1).
 //
 //   out[b][w] += sum_{k < rows} S[b][k] * T[k][w]   (mod 2^32)
 //

@@ -1,8 +1,7 @@
 // Share matrix x table mod 2^32 on the fifth-generation tensor cores
 // (tcgen05.mma, accumulators in tensor memory), exactly: the product of the
-// unfused baseline (paper Sec. 3.1: the B x L share matrix and the L x W
-// table "batched together as a single matrix-matrix multiplication"; Sec.
-// 3.2.2) for batches that make it a dense contraction.
+// unfused baseline (paper Sec. 3.1: the B x L share matrix times the L x W
+// table as one matrix-matrix product; Sec. 3.2.2) for batches that make it a dense contraction.
 //
 //   out[b][w] += sum_{k < K} S[b][k] * T[k][w]   (mod 2^32)
 //

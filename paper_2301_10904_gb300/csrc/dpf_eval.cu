@@ -40,7 +40,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 
+#include "async_copy.cuh"
 #include "internal.h"
 
 namespace pir {
@@ -75,8 +77,35 @@ constexpr int kHdrOff = kYOff + 4 * kYRegionWords;
 constexpr int kMaxGroup = 8;
 constexpr int kHdrBytes = 48 * kMaxGroup;                  // per query slot: QueryHdr
 constexpr int kItemOff = kHdrOff + kHdrBytes;              // work-item index broadcast (multi-table kernel)
-constexpr int kSmemBytes = kItemOff + 16;
+// Staged table scan (fused_eval_staged_kernel): one more warp issues bulk
+// copies of the table rows into a ring of shared-memory stages, each stage one
+// level of the DFS stack that the launch's subtrees leave unused (stage s is
+// level kStackLevels - s).  Its full and empty mbarriers and an abort flag
+// follow the work-item slot.
+constexpr int kIssuerThreads = 32;
+constexpr int kStagedThreads = kFusedThreads + kIssuerThreads;
+constexpr uint32_t kRingStageBytes = kProducers * 16;      // one stack level
+constexpr int kRingMaxStages = kStackLevels - 1;           // level 1 always holds staged keys
+constexpr int kRingBarOff = kItemOff + 16;                 // full[s] at +8s, empty[s] at +8(kRingMaxStages + s)
+constexpr int kRingAbortOff = kRingBarOff + 16 * kRingMaxStages;
+constexpr int kSmemBytes = kRingAbortOff + 16;
+static_assert(kRingBarOff % 8 == 0, "mbarriers need 8-byte alignment");
 static_assert(kSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
+// Polls of a bounded mbarrier wait in the staged scan (each try_wait may also
+// suspend the thread): far beyond any copy's latency, short of a hang.
+constexpr uint32_t kRingSpinLimit = 1u << 22;
+// Widest table row (words) the staged scan takes: four runs of a leaf pair must
+// fit one stage.
+constexpr uint64_t kRingMaxStride = kRingStageBytes / (4u * 2u * 4u);
+#ifndef PIR_RING_MIN_PHASES
+#define PIR_RING_MIN_PHASES 4
+#endif
+#ifndef PIR_RING_FENCE
+#define PIR_RING_FENCE 1
+#endif
+#ifndef PIR_RING_PREFETCH_DEFAULT
+#define PIR_RING_PREFETCH_DEFAULT 16
+#endif
 
 // The kernel's only shared memory; naming the array (not a pointer to it) in
 // every access lets the compiler address it as shared.
@@ -113,6 +142,12 @@ struct FusedParams {
     uint32_t shares_vec;  // 1 when shares and ld allow 16-byte stores
     // bins mode (partial batch retrieval): query q covers rows [q*bin_rows, ...)
     uint64_t bin_rows;
+    // staged scan: ring stages (2..kRingMaxStages), chunks the issuing warp
+    // prefetches into L2 ahead of the one it copies, and the library's device
+    // fault word (a wait that gives up sets PIR_FAULT_WAIT_TIMEOUT there)
+    uint32_t ring_stages;
+    uint32_t ring_prefetch;
+    uint32_t* faults;
 };
 
 struct QueryHdr {  // one per query slot of the current item, in shared memory
@@ -408,7 +443,21 @@ __device__ __forceinline__ void prefetch_l2(const void* addr, uint32_t bytes) {
 
 // Table rows that one hand-off phase multiplies, per CTA, above which the
 // next phase is not prefetched (all CTAs' two phases in flight must fit L2).
-constexpr uint32_t kPrefetchMaxBytes = 256u * 1024u;
+#ifndef PIR_PF_MAX_KIB
+#define PIR_PF_MAX_KIB 256
+#endif
+#ifndef PIR_PF_AHEAD
+#define PIR_PF_AHEAD 1
+#endif
+#ifndef PIR_PF_EARLY
+#define PIR_PF_EARLY 0
+#endif
+constexpr uint32_t kPrefetchMaxBytes = PIR_PF_MAX_KIB * 1024u;
+// Phases whose rows are asked of L2 ahead of the one being multiplied, and
+// whether the first of them are asked for at the start of the item (while its
+// path walk and split run) rather than when the consumers start.
+constexpr uint32_t kPfAhead = PIR_PF_AHEAD;
+constexpr bool kPfEarly = PIR_PF_EARLY != 0;
 
 // Consumers ask L2 for the rows of leaf pairs kbase..kbase+kc-1 of every
 // subtree ahead of the phase that multiplies them: per subtree one run of 2kc
@@ -451,6 +500,14 @@ __device__ __forceinline__ void prefetch_rows(const FusedParams& p, uint64_t r0,
         prefetch_phase(p, r0, m, nsub, kbase, kc, ct);
 }
 
+// Table rows a consumer thread has in flight when an item holds one or two
+// queries (the scan is then as heavy as the expansion): a multiple of 4.
+#ifndef PIR_SMALLG_ROWS
+#define PIR_SMALLG_ROWS 8
+#endif
+constexpr int kSmallGroupRows = PIR_SMALLG_ROWS;
+static_assert(kSmallGroupRows % 4 == 0, "rows in flight in groups of four");
+
 // Named barriers between producers and consumers: kBarFull + b marks share
 // buffer b as filled, kBarFree + b as consumed (barrier 0 is __syncthreads).
 constexpr int kBarFull = 1, kBarFree = 3;
@@ -473,7 +530,7 @@ __device__ __forceinline__ void mac_rows_grouped(const FusedParams& p, const uin
                                                  uint32_t rg, uint32_t nrg) {
     static_assert(R == 2 || R == 4, "rows per group");
     constexpr int SQ = kProducers / G;
-    constexpr int UG = (G <= 2 ? 8 : 4) / R;
+    constexpr int UG = (G <= 2 ? kSmallGroupRows : 4) / R;
     const uint32_t submask = (1u << sd) - 1u;
     const uint32_t ngroups = nrows / R;
     for (uint32_t q0 = rg; q0 < ngroups; q0 += UG * nrg) {
@@ -552,7 +609,7 @@ __device__ __forceinline__ void mac_phase(const FusedParams& p, const uint32_t* 
         mac_rows_grouped<G, VEC, 2>(p, yb, r0, m, sd, kbase, nrows, acc, c, rg, nrg);
         return;
     }
-    constexpr int U = G <= 2 ? 8 : 4;
+    constexpr int U = G <= 2 ? kSmallGroupRows : 4;
     for (uint32_t rr0 = rg; rr0 < nrows; rr0 += U * nrg) {
         uint32_t tv[U][VEC];
         uint32_t yi[U];
@@ -633,6 +690,178 @@ __device__ __forceinline__ void mac_phase_bins(const FusedParams& p, const uint3
     }
 }
 
+// ---------------------------------------------------------------- staged scan
+// The rows one hand-off phase multiplies are, for every subtree l of the item,
+// one run of 2kc consecutive rows (leaf pairs kbase..kbase+kc-1 of subtree l).
+// The staged kernel moves them into shared memory with the bulk-copy engine:
+// chunk ch of a phase is the runs of subtrees ch*rpc .. ch*rpc+rpc-1, one ring
+// stage each, and chunks go through the ring phase by phase.
+struct RingGeom {
+    uint32_t kc;   // leaf pairs per subtree per phase
+    uint32_t rpc;  // runs per chunk: a power of two, at least 4
+    uint32_t nch;  // chunks per phase
+    bool on;       // whether this item's table scan goes through the ring
+};
+
+// For an item whose subtrees are 2^m rows deep, 2^sd of them.  Both the
+// issuing warp and the consumers derive it, so they walk the same chunks.
+__device__ __forceinline__ RingGeom ring_geom(const FusedParams& p, int sd, int m) {
+    RingGeom g{};
+    const uint32_t npairs = 1u << (m - 1);
+    uint32_t kc = max(1u, min((uint32_t)kPairs, npairs / PIR_RING_MIN_PHASES));
+    const uint32_t pair_bytes = 2u * (uint32_t)p.stride * 4u;  // one leaf pair's rows
+    while (kc > 1 && 4u * kc * pair_bytes > kRingStageBytes) kc >>= 1;
+    const uint32_t fit = kRingStageBytes / (kc * pair_bytes);
+    uint32_t rpc = fit ? 1u << (31 - __clz(fit)) : 0u;
+    rpc = min(rpc, 1u << sd);
+    g.kc = kc;
+    g.rpc = rpc;
+    g.nch = rpc ? (1u << sd) / rpc : 0u;
+    g.on = p.ring_stages >= 2 && rpc >= 4;
+    return g;
+}
+
+__device__ __forceinline__ char* ring_stage(uint32_t s) {
+    return sm + kStackOff + (kStackLevels - 1 - (int)s) * (int)kRingStageBytes;
+}
+__device__ __forceinline__ uint32_t ring_full(uint32_t s) { return smem_addr(sm + kRingBarOff) + 8u * s; }
+__device__ __forceinline__ uint32_t ring_empty(uint32_t s) {
+    return smem_addr(sm + kRingBarOff) + 8u * (kRingMaxStages + s);
+}
+__device__ __forceinline__ volatile uint32_t* ring_abort() {
+    return reinterpret_cast<volatile uint32_t*>(sm + kRingAbortOff);
+}
+
+// The part of run u of chunk ch inside [row_lo, row_hi): its first row and the
+// bytes of its span (zero when the run lies outside).
+__device__ __forceinline__ uint32_t ring_run(const FusedParams& p, uint64_t r0, int m, uint32_t kbase,
+                                             const RingGeom& g, uint32_t ch, uint32_t u, uint64_t& first,
+                                             uint32_t& skip) {
+    const uint64_t a = r0 + ((uint64_t)(ch * g.rpc + u) << m) + 2ull * kbase;
+    const uint64_t b = a + 2ull * g.kc;
+    const uint64_t lo = a > p.row_lo ? a : p.row_lo, hi = b < p.row_hi ? b : p.row_hi;
+    first = lo;
+    skip = (uint32_t)(lo - a);
+    return lo < hi ? (uint32_t)(((hi - lo - 1) * p.stride + p.width) * 4u) : 0u;
+}
+
+// Issuing warp: chunk ch of the phase at leaf pair kbase into ring stage s.
+// Lane 0 arrives on the stage's full barrier with the chunk's byte count, then
+// every lane starts the copies of its runs (rpc <= 512, so at most 16 each).
+// Table rows and their copies in shared memory keep the table's row pitch.
+__device__ __forceinline__ void ring_issue(const FusedParams& p, uint64_t r0, int m, uint32_t kbase,
+                                           const RingGeom& g, uint32_t ch, uint32_t s, uint32_t lane) {
+    const uint32_t bar = ring_full(s);
+    const uint32_t dst0 = smem_addr(ring_stage(s));
+    const uint32_t row_bytes = (uint32_t)p.stride * 4u;
+    uint32_t total = 0;
+    for (uint32_t u = lane; u < g.rpc; u += 32) {
+        uint64_t first;
+        uint32_t skip;
+        total += ring_run(p, r0, m, kbase, g, ch, u, first, skip);
+    }
+    total = __reduce_add_sync(0xffffffffu, total);
+    if (lane == 0) mbar_expect_tx(bar, total);
+    __syncwarp();
+    for (uint32_t u = lane; u < g.rpc; u += 32) {
+        uint64_t first;
+        uint32_t skip;
+        const uint32_t bytes = ring_run(p, r0, m, kbase, g, ch, u, first, skip);
+        if (bytes)
+            bulk_g2s(dst0 + (u * 2u * g.kc + skip) * row_bytes, p.table + (first - p.row_lo) * p.stride, bytes, bar);
+    }
+}
+
+// The same rows asked of L2 ahead of their copy (the copy engine fetches them
+// while the ring is still full).
+__device__ __forceinline__ void ring_prefetch(const FusedParams& p, uint64_t r0, int m, uint32_t kbase,
+                                              const RingGeom& g, uint32_t ch, uint32_t lane) {
+    for (uint32_t u = lane; u < g.rpc; u += 32) {
+        uint64_t first;
+        uint32_t skip;
+        const uint32_t bytes = ring_run(p, r0, m, kbase, g, ch, u, first, skip);
+        if (bytes) prefetch_l2(p.table + (first - p.row_lo) * p.stride, bytes);
+    }
+}
+
+// Consumer thread ct: multiply chunk ch of the phase at leaf pair kbase (ring
+// stage `stage`, shares in yb) into acc.  Consumer (c, rg) owns words
+// 4c..4c+3; it takes groups of four runs u..u+3 at the same row j of their
+// runs, whose shares are adjacent for every query (one 128-bit load each).
+template <int G>
+__device__ __forceinline__ void mac_chunk(const FusedParams& p, const uint32_t* yb, const char* stage, uint64_t r0,
+                                          int m, uint32_t kbase, const RingGeom& g, uint32_t ch,
+                                          uint32_t (&acc)[G][4], uint32_t ct) {
+    constexpr int SQ = kProducers / G;
+    const uint32_t nc = p.width / 4u;
+    const uint32_t nrg = kConsumers / nc;
+    const uint32_t c = ct % nc, rg = ct / nc;
+    if (rg >= nrg) return;
+    const uint32_t two_kc = 2u * g.kc;
+    const uint32_t ngroups = (g.rpc / 4u) * two_kc;
+    const uint32_t row_bytes = (uint32_t)p.stride * 4u;
+    for (uint32_t q = rg; q < ngroups; q += nrg) {
+        const uint32_t j = q & (two_kc - 1u), u = (q / two_kc) * 4u;
+        const uint32_t l = ch * g.rpc + u;
+        uint4 t[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint64_t row = r0 + ((uint64_t)(l + h) << m) + 2ull * kbase + j;
+            t[h] = (row >= p.row_lo && row < p.row_hi)
+                       ? *reinterpret_cast<const uint4*>(stage + ((u + h) * two_kc + j) * row_bytes + c * 16u)
+                       : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            const uint4 y = *reinterpret_cast<const uint4*>(yb + (a * 2 * kPairs + j) * SQ + l);
+            acc[a][0] += y.x * t[0].x + y.y * t[1].x + y.z * t[2].x + y.w * t[3].x;
+            acc[a][1] += y.x * t[0].y + y.y * t[1].y + y.z * t[2].y + y.w * t[3].y;
+            acc[a][2] += y.x * t[0].z + y.y * t[1].z + y.z * t[2].z + y.w * t[3].z;
+            acc[a][3] += y.x * t[0].w + y.y * t[1].w + y.z * t[2].w + y.w * t[3].w;
+        }
+    }
+}
+
+// Position in the ring over the launch: chunks passed (the same count in the
+// issuing warp and in every consumer) and, in the issuing warp, one past the
+// last chunk whose copies it started.
+struct RingState {
+    uint32_t seq = 0;
+    uint32_t issued = 0;
+};
+
+// Issuing warp: chunks k0 .. k1-1 of the item (phase-major), each into stage
+// seq % S after the consumers have released that stage's previous use.  A wait
+// that gives up records the fault and stops all further copies of the CTA.
+__device__ __forceinline__ void ring_issue_range(const FusedParams& p, uint64_t r0, int m, const RingGeom& g,
+                                                 uint32_t k0, uint32_t k1, uint32_t ktotal, RingState& rs,
+                                                 uint32_t lane) {
+    const uint32_t S = p.ring_stages;
+    for (uint32_t k = k0; k < k1; ++k, ++rs.seq) {
+        const uint32_t seq = rs.seq;
+        if (*ring_abort()) continue;
+        const uint32_t s = seq % S, round = seq / S;
+        if (round >= 1) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(ring_empty(s), (round - 1u) & 1u, kRingSpinLimit);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) {
+                    atomicOr(p.faults, PIR_FAULT_WAIT_TIMEOUT);
+                    *ring_abort() = 1u;
+                }
+                __syncwarp();
+                continue;
+            }
+        }
+        if (PIR_RING_FENCE) fence_proxy_async_smem();  // the consumers' reads of the stage before its refill
+        ring_issue(p, r0, m, (k / g.nch) * g.kc, g, k % g.nch, s, lane);
+        rs.issued = seq + 1u;
+        const uint32_t kp = k + p.ring_prefetch;
+        if (p.ring_prefetch && kp < ktotal) ring_prefetch(p, r0, m, (kp / g.nch) * g.kc, g, kp % g.nch, lane);
+    }
+}
+
 // Writes this thread's last 2*kc leaf shares (rows row_base .. row_base+2kc-1)
 // to the materialised share matrix.
 template <int G>
@@ -659,12 +888,16 @@ __device__ __forceinline__ void store_phase(const FusedParams& p, const uint32_t
 // 2^r rows starting at r0 (1 <= r <= n).  MAT = false: fused share x table product (a1-a6)
 // with kConsumers consumer threads after the kProducers producers;
 // MAT = true: producers only, leaf shares written to each slot's `out`.
+// STAGED: a last warp copies the table rows into the shared-memory ring and the
+// consumers multiply them from there; `seq` counts the ring's chunks over the
+// launch (the same in the issuing warp and every consumer).
 // Ends with a barrier, so shared memory is free for the next item.
-template <int G, int VEC, bool MAT, bool BINS>
-__device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int r) {
+template <int G, int VEC, bool MAT, bool BINS, bool STAGED = false>
+__device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int r, RingState& rs) {
     constexpr int SQ = kProducers / G;
     constexpr int LOG_SQ = (SQ == 512) ? 9 : (SQ == 256) ? 8 : (SQ == 128) ? 7 : 6;
-    constexpr int NT = MAT ? kProducers : kFusedThreads;
+    constexpr int NT = MAT ? kProducers : STAGED ? kStagedThreads : kFusedThreads;
+    static_assert(!STAGED || (VEC == 4 && !MAT && !BINS && G <= 4), "staged scan: 128-bit rows, fused, G <= 4");
     static_assert(G * 2 * kPairs * SQ * 2 <= kYWords, "share buffers exceed their region");
     static_assert(2 * kProducers * (int)sizeof(uint4) <= 4 * kYRegionWords, "split buffers exceed their region");
     static_assert(kMaxGroup * 512 <= kYRegionWords, "reduction of the widest supported rows exceeds its region");
@@ -672,11 +905,46 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
 
     const int tid = threadIdx.x;
     const bool producer = tid < kProducers;
+    const bool issuer = STAGED && tid >= kFusedThreads;
     const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
     uint32_t* ybuf = reinterpret_cast<uint32_t*>(sm + kYOff);
     const int n = (int)p.n;
     const int sd = min(LOG_SQ, r - 1);
     const int m = r - sd;
+    const uint32_t npairs = 1u << (m - 1);
+    RingGeom ring{};
+    if constexpr (STAGED) ring = ring_geom(p, sd, m);
+    // chunks of this item in the ring, and how many the issuing warp starts
+    // before the path walk (the ring is empty between items, so those need no wait)
+    const uint32_t ring_chunks = ring.on ? (npairs / ring.kc) * ring.nch : 0u;
+    const uint32_t ring_early = min(ring_chunks, STAGED ? p.ring_stages : 0u);
+    if (issuer && ring.on) {
+        const uint32_t lane = (uint32_t)tid & 31u;
+        ring_issue_range(p, r0, m, ring, 0, ring_early, ring_chunks, rs, lane);
+    }
+    const int nsub = 1 << sd;
+    // leaf pairs per hand-off: at most kPairs, and small enough that an item has
+    // four phases where it can, so that the scan of one phase overlaps the
+    // expansion of the next even when an item is small
+    uint32_t kc = ring.on ? ring.kc : max(1u, min((uint32_t)kPairs, npairs >> 2));
+    // With one or two queries per item the table scan weighs as much as the
+    // expansion: the consumers then have the copy engine prefetch the rows of
+    // the phases kPfAhead ahead into L2, with phases small enough that
+    // kPfAhead + 1 of every CTA's fit there; the first ones while the item's
+    // path walk and split run.  (With more queries per item the rows are
+    // reused G times and the prefetch only costs issue slots.)
+    bool pf = false;
+    if ((G <= 2 || BINS) && VEC == 4 && !MAT && !ring.on) {
+        // bins mode: every slot reads its own rows, so the scan never amortises
+        const uint64_t pair_bytes = (BINS ? (uint64_t)G : 1u) * nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
+        while (kc > 1 && pair_bytes * kc > kPrefetchMaxBytes) kc >>= 1;
+        pf = pair_bytes * kc <= kPrefetchMaxBytes;
+    }
+    const uint32_t nphases = npairs / kc;
+    const uint32_t pf_first = pf ? min(nphases, (uint32_t)kPfAhead) : 0u;
+    if (kPfEarly && pf && !producer && !issuer)
+        for (uint32_t a = 0; a < pf_first; ++a)
+            prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, a * kc, kc, (uint32_t)(tid - kProducers));
 
     // ---- stage the group's keys in shared memory ---------------------------
     {
@@ -747,25 +1015,6 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
         }
         __syncthreads();
     }
-    const int nsub = 1 << sd;
-    const uint32_t npairs = 1u << (m - 1);
-    // leaf pairs per hand-off: at most kPairs, and small enough that an item has
-    // four phases where it can, so that the scan of one phase overlaps the
-    // expansion of the next even when an item is small
-    uint32_t kc = max(1u, min((uint32_t)kPairs, npairs >> 2));
-    // With one or two queries per item the table scan weighs as much as the
-    // expansion: the consumers then have the copy engine prefetch the next
-    // phase's rows into L2, with phases small enough that two of every CTA's
-    // fit there.  (With more queries per item the rows are reused G times and
-    // the prefetch only costs issue slots.)
-    bool pf = false;
-    if constexpr ((G <= 2 || BINS) && VEC == 4 && !MAT) {
-        // bins mode: every slot reads its own rows, so the scan never amortises
-        const uint64_t pair_bytes = (BINS ? (uint64_t)G : 1u) * nsub * 2u * p.stride * 4u;  // one leaf pair of every subtree
-        while (kc > 1 && pair_bytes * kc > kPrefetchMaxBytes) kc >>= 1;
-        pf = pair_bytes * kc <= kPrefetchMaxBytes;
-    }
-    const uint32_t nphases = npairs / kc;
     const int g = producer ? tid / SQ : 0, l = producer ? tid % SQ : 0;
     const QueryHdr* hq = hdr_slot(g);
     const bool act = producer && l < nsub && hq->ok != 0;
@@ -829,12 +1078,40 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
                 ++lvl;
             }
         }
+    } else if (issuer) {
+        // ---- issuing warp: the rest of the item's chunks, as stages free up ----
+        if (ring.on) ring_issue_range(p, r0, m, ring, ring_early, ring_chunks, ring_chunks, rs, (uint32_t)tid & 31u);
+    } else if (STAGED && ring.on) {
+        if constexpr (STAGED) {
+            // ---- consumers, staged: every chunk of a filled buffer from its ring stage ----
+            const uint32_t ct = (uint32_t)(tid - kProducers), lane = (uint32_t)tid & 31u;
+            const uint32_t S = p.ring_stages;
+            for (uint32_t ph = 0; ph < nphases; ++ph) {
+                bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
+                const uint32_t* yb = ybuf + (ph & 1u) * (kYWords / 2);
+                for (uint32_t ch = 0; ch < ring.nch; ++ch, ++rs.seq) {
+                    const uint32_t st = rs.seq % S;
+                    if (!*ring_abort() && !mbar_wait_bounded(ring_full(st), (rs.seq / S) & 1u, kRingSpinLimit)) {
+                        if (lane == 0) atomicOr(p.faults, PIR_FAULT_WAIT_TIMEOUT);
+                        *ring_abort() = 1u;
+                    }
+                    // after a failed wait the stages hold nothing trustworthy: keep the
+                    // barriers' counts, skip the arithmetic
+                    if (!*ring_abort()) mac_chunk<G>(p, yb, ring_stage(st), r0, m, ph * kc, ring, ch, acc, ct);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ring_empty(st));
+                }
+                if (ph + 2 < nphases) bar_arrive(kBarFree + (int)(ph & 1u), kFusedThreads);
+            }
+        }
     } else if constexpr (!MAT) {
         // ---- consumers: multiply every filled buffer into the accumulators ----
         const uint32_t ct = (uint32_t)(tid - kProducers);
-        if (pf) prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, 0, kc, ct);
+        if (!kPfEarly)
+            for (uint32_t a = 0; a < pf_first; ++a) prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, a * kc, kc, ct);
         for (uint32_t ph = 0; ph < nphases; ++ph) {
-            if (pf && ph + 1 < nphases) prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, (ph + 1) * kc, kc, ct);
+            if (pf && ph + kPfAhead < nphases)
+                prefetch_rows<G, BINS>(p, r0, m, (uint32_t)nsub, (ph + kPfAhead) * kc, kc, ct);
             bar_sync(kBarFull + (int)(ph & 1u), kFusedThreads);
             if constexpr (BINS)
                 mac_phase_bins<G>(p, ybuf + (ph & 1u) * (kYWords / 2), r0, m, sd, ph * kc, kc, acc, ct);
@@ -851,7 +1128,9 @@ __device__ __forceinline__ void run_item(const FusedParams& p, uint64_t r0, int 
     uint32_t* red = ybuf;
     for (uint32_t i = tid; i < G * W; i += NT) red[i] = 0;
     __syncthreads();
-    if (!producer && BINS) {
+    if (issuer) {
+        // the issuing warp holds no partial sums
+    } else if (!producer && BINS) {
         // team g holds slot g's partial sums in acc[0]
         const uint32_t ct = (uint32_t)(tid - kProducers);
         constexpr uint32_t kTeam = kConsumers / G;
@@ -918,9 +1197,18 @@ __device__ __forceinline__ void divmod(uint64_t a, uint64_t b, uint64_t& q, uint
 // nfull items (whole rounds of the grid) run whole; each later one is cut into
 // 2^tail_log2 pieces, so that the last round keeps every CTA busy.  Pieces with
 // the same index run side by side, again query groups fastest.
-template <int G, int VEC, bool MAT, bool BINS>
+template <int G, int VEC, bool MAT, bool BINS, bool STAGED = false>
 __device__ __forceinline__ void eval_items(const FusedParams& p) {
     if (!smem_base_ok(p.status)) return;
+    RingState rs;
+    if (STAGED && threadIdx.x == 0) {
+        for (uint32_t st = 0; st < p.ring_stages; ++st) {
+            mbar_init(ring_full(st), 1);                // the issuing lane's arrival + the copies' bytes
+            mbar_init(ring_empty(st), kConsumers / 32);  // one arrival per consumer warp
+        }
+        *ring_abort() = 0u;
+        fence_mbarrier_init();
+    }  // (build_tables ends with a CTA barrier)
     // (the launch parameters are read before the tables are built, so that their
     // first constant-cache misses overlap the fill)
     const uint64_t rest = p.nitems - p.nfull;
@@ -958,13 +1246,30 @@ __device__ __forceinline__ void eval_items(const FusedParams& p) {
                 h->out = valid ? p.out + (uint64_t)q * p.width : nullptr;
         }
         __syncthreads();
-        run_item<G, VEC, MAT, BINS>(p, r0, r);
+        run_item<G, VEC, MAT, BINS, STAGED>(p, r0, r, rs);
+    }
+    if (STAGED && threadIdx.x >= kFusedThreads && *ring_abort()) {
+        // copies may still be landing after an abort: see this warp's last ones
+        // in (bounded) before the CTA's shared memory goes to the next CTA
+        const uint32_t S = p.ring_stages;
+        const uint32_t first = rs.issued > S ? rs.issued - S : 0u;
+        if ((threadIdx.x & 31) == 0)
+            for (uint32_t k = first; k < rs.issued; ++k)
+                mbar_wait_bounded(ring_full(k % S), (k / S) & 1u, kRingSpinLimit);
+        __syncwarp();
     }
 }
 
 template <int G, int VEC>
 __global__ void __launch_bounds__(kFusedThreads, 1) fused_eval_kernel(const FusedParams p) {
     eval_items<G, VEC, false, false>(p);
+}
+
+// The fused kernel with its table scan staged through shared memory by the
+// bulk-copy engine (one more warp issues the copies; 128-bit rows, G <= 4).
+template <int G>
+__global__ void __launch_bounds__(kStagedThreads, 1) fused_eval_staged_kernel(const FusedParams p) {
+    eval_items<G, 4, false, false, true>(p);
 }
 
 // Partial batch retrieval: G bins per work item, each slot with its own rows.
@@ -1012,11 +1317,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const Mult
         __syncthreads();
         const uint64_t r0 = w.range << tb.range_log2;
         const int r = (int)tb.range_log2;
+        RingState rs;  // (no ring here)
         switch (w.group) {  // uniform over the CTA
-            case 1: run_item<1, VEC, false, false>(p, r0, r); break;
-            case 2: run_item<2, VEC, false, false>(p, r0, r); break;
-            case 4: run_item<4, VEC, false, false>(p, r0, r); break;
-            default: run_item<kMaxGroup, VEC, false, false>(p, r0, r); break;
+            case 1: run_item<1, VEC, false, false>(p, r0, r, rs); break;
+            case 2: run_item<2, VEC, false, false>(p, r0, r, rs); break;
+            case 4: run_item<4, VEC, false, false>(p, r0, r, rs); break;
+            default: run_item<kMaxGroup, VEC, false, false>(p, r0, r, rs); break;
         }
     }
 }
@@ -1127,6 +1433,25 @@ uint32_t plan_tail_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t gro
     const uint32_t nqg = (batch + group - 1) / group;
     const uint64_t items = items_for(row_lo, rows, range_log2, nqg);
     return (uint32_t)pick_tail_log2(items, std::max(1, device_sm_count()), n, group, (int)range_log2);
+}
+
+// Ring stages of a staged launch of this plan: the DFS stack levels that its
+// subtrees (at most 2^m rows deep, the whole items' depth) and its staged keys
+// leave free, at most kRingMaxStages.
+static int ring_stages_for(const pir_plan& plan) {
+    const int r = (int)plan.range_log2;
+    const int m = r - std::min(log_sq(plan.group), r - 1);
+    const int key_levels =
+        (int)((plan.group * (uint32_t)dev::kKeySlotBytes + dev::kRingStageBytes - 1) / dev::kRingStageBytes);
+    return std::min(dev::kRingMaxStages, dev::kStackLevels - std::max(m - 1, key_levels));
+}
+
+int plan_check_staged(const pir_plan& plan, uint32_t n, uint32_t width, uint64_t stride, bool vec_ok) {
+    const int rc = plan_check(plan, n, width, vec_ok);
+    if (rc != PIR_OK) return rc;
+    if (plan.vec != 4 || plan.group > 4 || stride > dev::kRingMaxStride || ring_stages_for(plan) < 2)
+        return PIR_ERR_UNSUPPORTED;
+    return PIR_OK;
 }
 
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
@@ -1292,13 +1617,39 @@ int launch_bins(const EvalRequest& req, uint64_t bin_rows, const pir_plan& plan,
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "bins_eval launch");
 }
 
+// Chunks of the staged scan that the issuing warp asks L2 for ahead of the one
+// it copies (0: none).  A tuning knob: PIR_RING_PREFETCH_CHUNKS in the
+// environment overrides the default, read once per process.
+static uint32_t ring_prefetch_chunks() {
+    static const uint32_t v = [] {
+        const char* e = std::getenv("PIR_RING_PREFETCH_CHUNKS");
+        return e ? (uint32_t)std::strtoul(e, nullptr, 10) : (uint32_t)PIR_RING_PREFETCH_DEFAULT;
+    }();
+    return v;
+}
+
 int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream) {
     if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
-    const dev::FusedParams p = make_params(req, plan);
+    dev::FusedParams p = make_params(req, plan);
     if (p.nitems == 0) return PIR_OK;
     const uint32_t ctas = grid_for(p.nitems);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
+    if (plan.strategy == PIR_STRATEGY_FUSED_STAGED) {
+        if (plan_check_staged(plan, req.n, req.width, req.stride, plan.vec == 4) != PIR_OK ||
+            (reinterpret_cast<uintptr_t>(req.table) & 15u) != 0 || req.stride % 4 != 0)
+            return PIR_ERR_UNSUPPORTED;
+        p.ring_stages = (uint32_t)ring_stages_for(plan);
+        p.ring_prefetch = ring_prefetch_chunks();
+        p.faults = device_fault_word();
+        if (!p.faults) return cuda_fail((int)cudaGetLastError(), "fault word address");
+        switch (plan.group) {
+            case 1: e = dev::launch_kernel(dev::fused_eval_staged_kernel<1>, p, ctas, dev::kStagedThreads, s); break;
+            case 2: e = dev::launch_kernel(dev::fused_eval_staged_kernel<2>, p, ctas, dev::kStagedThreads, s); break;
+            default: e = dev::launch_kernel(dev::fused_eval_staged_kernel<4>, p, ctas, dev::kStagedThreads, s); break;
+        }
+        return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "fused_eval_staged launch");
+    }
     if (plan.vec == 4) {
         switch (plan.group) {
             case 1: e = dev::launch_kernel(dev::fused_eval_kernel<1, 4>, p, ctas, dev::kFusedThreads, s); break;

@@ -103,6 +103,9 @@ int plan_fused_sms(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_
 int plan_fused(uint64_t rows_evaluated, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan);
 int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok);
+// The same for PIR_STRATEGY_FUSED_STAGED, which also needs the table's row
+// pitch (words) and leaves room for its shared-memory ring.
+int plan_check_staged(const pir_plan& plan, uint32_t n, uint32_t width, uint64_t stride, bool vec_ok);
 // Pieces per cut item of the last, partial round (log2) for a plan's shape.
 uint32_t plan_tail_log2(uint64_t row_lo, uint64_t rows, uint32_t n, uint32_t group, uint32_t batch,
                         uint32_t range_log2);

@@ -1,6 +1,6 @@
 // Share matrix x table mod 2^32 for a few queries: a streaming scan of the
 // table, bound by HBM bandwidth.  With a small batch the product of Sec. 3.1
-// ("batched together as a single matrix-matrix multiplication") does a few
+// (a batch of queries to one table is one matrix-matrix product) does a few
 // multiply-adds per table byte, so every table row should leave HBM once, at
 // full bandwidth (Sec. 3.2.4: the table read is the memory-bound part).
 //
@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "internal.h"
 
 namespace pir {
@@ -61,39 +62,12 @@ struct ScanParams {
 
 extern __shared__ __align__(128) char scan_sm[];
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 // bounded wait for the phase with the given parity to complete
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kScanSpinLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    return mbar_wait_bounded(bar, parity, kScanSpinLimit);
 }
 __device__ __forceinline__ void consumers_sync() {
     asm volatile("bar.sync %0, %1;" ::"n"(kScanConsumerBar), "n"(kScanConsumers) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
 }
 
 // Thread 0: start the copies of chunk c into stage s.  Table rows
@@ -151,7 +125,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) contract_scan_kernel(const Sc
             mbar_init(empty0 + 8u * s, kScanConsumerWarps);   // one arrival per consumer warp
         }
         *abort_flag = 0u;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_mbarrier_init();
     }
     __syncthreads();  // the only CTA-wide barrier
     // this CTA's chunks, c_first + j * c_step for c < c_end: dealt round-robin, or
@@ -172,7 +146,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) contract_scan_kernel(const Sc
                     *abort_flag = 1u;
                     break;  // stop issuing; the consumers' bounded waits run out
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // consumers' reads before the refill
+                fence_proxy_async_smem();  // consumers' reads before the refill
                 scan_issue(p, s, c);
             }
             // the copies of the last stages issued are this thread's: see them land (bounded)
@@ -259,7 +233,7 @@ __global__ void wait_selftest_kernel(uint32_t polls, uint32_t* gave_up) {
     if (threadIdx.x != 0) return;
     const uint32_t b = smem_addr(&bar);
     mbar_init(b, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbarrier_init();
     bool done = false;
     for (uint32_t i = 0; i < polls && !done; ++i) done = mbar_try_wait(b, 0);
     if (!done) atomicOr(&g_device_faults, PIR_FAULT_WAIT_TIMEOUT);

@@ -201,7 +201,8 @@ def test_autotuner_weighs_expand_and_scan_for_few_queries(env):
     dk = dev_keys(torch, ks0)
     out = torch.empty((batch, width), dtype=torch.int32, device="cuda")
     plan, ms = pir.pir_autotune(table, dk, batch, out)
-    assert ms > 0 and plan.strategy in (pir.PIR_STRATEGY_FUSED, pir.PIR_STRATEGY_EXPAND_SCAN)
+    assert ms > 0 and plan.strategy in (pir.PIR_STRATEGY_FUSED, pir.PIR_STRATEGY_EXPAND_SCAN,
+                                        pir.PIR_STRATEGY_FUSED_STAGED)
     chosen = pir.pir_plan_for(rows, width, batch)
     assert (chosen.strategy, chosen.group, chosen.range_log2) == (plan.strategy, plan.group, plan.range_log2)
     got = run_device(torch, pir, table, ks0, width)

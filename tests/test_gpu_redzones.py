@@ -92,21 +92,29 @@ def _answers(orc, keys, T, lo=0, hi=None):
     return np.stack([orc.answer(k, T, lo, hi) for k in keys])
 
 
-@pytest.mark.parametrize("strategy", [0, 1], ids=["fused", "expand_scan"])
+@pytest.mark.parametrize("strategy", [0, 1, 2], ids=["fused", "expand_scan", "fused_staged"])
 @pytest.mark.parametrize("rows,W,B,pad", [(4096 + 77, 16, 3, 4), (1 << 14, 64, 8, 4), (1000, 3, 5, 1),
-                                          (3000, 8, 9, 8), ((1 << 15) + 1000, 32, 2, 4), (2, 1, 1, 3)])
+                                          (3000, 8, 9, 8), ((1 << 15) + 1000, 32, 2, 4), (2, 1, 1, 3),
+                                          ((1 << 16) + 5, 64, 1, 4)])
 def test_server_eval_redzones(env, rows, W, B, pad, strategy):
     torch, pir, orc = env
     if strategy == 1 and (W % 4 or pad % 4 or B > 8):
         pytest.skip("the expand-and-scan strategy needs 16-byte rows and at most 8 queries")
+    if strategy == 2 and (W % 4 or pad % 4 or rows < 4):
+        pytest.skip("the staged scan needs 16-byte rows")
     n = pir.pir_domain_bits(rows)
     T = wl.table_u32(rows + 3, rows, W)
     ks0, _ = make_keys(orc, n, wl.alphas(rows + 5, rows, B), [1] * B, rows + 7)
     tbuf, table = guarded_table(torch, T, pad, 101)
     kbuf, dkeys = guarded_bytes(torch, b"".join(ks0), 202)
     obuf, out = guarded_out(torch, B, W, 303)
-    plan = pir.pir_plan_for(rows, W, B)
-    plan.strategy = strategy
+    if strategy == 2:
+        from test_gpu_staged import staged_plan
+
+        plan = staged_plan(pir, rows, W, B)
+    else:
+        plan = pir.pir_plan_for(rows, W, B)
+        plan.strategy = strategy
     pir.pir_server_eval_device_plan(table, dkeys, B, out, plan)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), _answers(orc, ks0, T))

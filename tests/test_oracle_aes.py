@@ -54,7 +54,7 @@ def test_cipher_matches_openssl_on_random_blocks(orc):
 
 
 def test_prf_is_aes_keyed_by_node_on_child_bit(orc):
-    # Sec. 3.1: PRF_s(x) "encrypts a message x with an encryption key s".
+    # Sec. 3.1, Eq. p3: PRF_s(x) is a cipher keyed by s applied to the message x.
     ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
     seed = bytes(range(16, 32))
     for x in (0, 1):

@@ -64,6 +64,11 @@ def test_bench_shapes_on_gb300(pir):
     assert shape(1 << 16, 16, 1) == (1, 9, 0, 128, 4, 0)           # one query on 2^16 x 16: fused
     assert shape((1 << 14) + 77, 16, 200) == (8, 11, 1, 152, 4, 0)
     assert shape(1 << 20, 64, 1)[5] == 1                           # a lone query on 256 MiB: expand + scan
+    assert shape(1 << 19, 64, 1)[5] == 1                           # 128 MiB of 64-word rows: expand + scan
+    assert shape(1 << 20, 128, 2)[5] == 1                          # two queries, 128-word rows: expand + scan
+    assert shape(1 << 20, 64, 2)[5] == 0                           # two queries, 64-word rows: fused
+    assert shape(1 << 24, 32, 1)[5] == 0                           # 32-word rows: fused, even at 2 GiB
+    assert shape(1 << 16, 256, 1)[5] == 0                          # wide rows, 64 MiB table: fused
     assert shape(1 << 20, 63, 1)[4:] == (1, 0)                     # unaligned rows: 32-bit loads, fused
 
 
