@@ -207,7 +207,12 @@ int pir_reconstruct(const uint32_t* s0, const uint32_t* s1, size_t w, uint32_t* 
  * memory from a pool the library creates per device, which keeps up to
  * 256 MiB of freed staging mapped between calls.  Errors: PIR_ERR_ARG,
  * PIR_ERR_KEY, PIR_ERR_DOMAIN, PIR_ERR_NOMEM, PIR_ERR_CUDA,
- * PIR_ERR_UNSUPPORTED. */
+ * PIR_ERR_UNSUPPORTED, and, with a host `out`, PIR_ERR_TIMEOUT when a
+ * bounded wait in this call's kernels gave up (the expand-and-scan and
+ * staged strategies have such waits; the shares are then incomplete and
+ * PIR_FAULT_WAIT_TIMEOUT stays set in the device status).  With a device
+ * `out` the call is asynchronous: check pir_device_status after
+ * synchronizing. */
 int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
 
 /* Same computation with keys and outputs already in device memory (the
@@ -222,7 +227,10 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
  * bytes from the library's pool and contracted by the streaming scan
  * (PIR_STRATEGY_EXPAND_SCAN; faster there on GB300, where each table row read
  * serves too few queries for the fused kernel's product side).  Same result
- * bit for bit.  Asynchronous on `stream`. */
+ * bit for bit.  Asynchronous on `stream`; the expand-and-scan and staged
+ * strategies' bounded waits report a wait that gave up only through
+ * PIR_FAULT_WAIT_TIMEOUT (pir_device_status), which callers check after
+ * synchronizing. */
 int pir_server_eval_device(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout,
                            uint32_t* dstatus, void* stream);
 
@@ -254,11 +262,14 @@ int pir_server_eval_range(const pir_table* shard, uint64_t row_lo, uint64_t doma
  * be <= 196608 and batch * width * 4 <= 65536, else PIR_ERR_UNSUPPORTED.
  * The call calls no device allocator and returns after `out` holds the
  * shares.  The first call on a device looks up the region's device address
- * (one-time set-up); make that first call before any stream capture.  All
- * calls share the region, which keeps the last call's contents (the share
- * area is cleared at the start of each call): calls that overlap on the GPU
- * race, so issue them from one stream and one thread at a time.
- * Errors: as pir_server_eval, plus PIR_ERR_UNSUPPORTED for the size limit. */
+ * (one-time set-up; repeated once if the device's primary context has been
+ * replaced, e.g. after cudaDeviceReset); make that first call before any
+ * stream capture.  All calls share the region, which keeps the last call's
+ * contents (the share area is cleared at the start of each call): calls that
+ * overlap on the GPU race, so issue them from one stream and one thread at a
+ * time.  `out` must be host memory (PIR_ERR_ARG for device or managed
+ * memory).  Errors: as pir_server_eval, plus PIR_ERR_UNSUPPORTED for the size
+ * limit. */
 int pir_server_eval_noalloc(const pir_table* t, const uint8_t* keys, size_t batch, uint32_t* out, void* stream);
 
 /* ---- many tables in one launch ------------------------------------- */
@@ -465,9 +476,11 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  *    200 KB of shared memory) holding its SM's tensor memory (512
  *    columns; 256 for 32-word tiles) while it runs, so a kernel that uses
  *    tensor memory on the same SM at the same time waits for it.  Its
- *    waits are bounded like the scan's;
- *    one that gives up leaves dout incomplete and sets
- *    PIR_FAULT_WAIT_TIMEOUT;
+ *    waits are bounded like the scan's; one that gives up sets
+ *    PIR_FAULT_WAIT_TIMEOUT, and then the whole launch's dout is invalid,
+ *    not only that CTA's tile: the CTA frees its tensor memory after a
+ *    last bounded wait for its own MMAs, which may still be writing there
+ *    when the next CTA on that SM allocates it;
  *  - PIR_CONTRACT_SCAN: for a few queries, where the product is bound by
  *    reading the table (Sec. 3.2.4): the copy engine streams table rows and
  *    share words through shared memory, eight queries per pass over the
@@ -510,10 +523,20 @@ int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_
                  pir_plan* plan, float* best_ms);
 
 /* Library-wide device fault bits, set by a kernel whose bounded wait gave
- * up (the kernel then returns early; its output is incomplete).  Reads the
- * bits of the current device (synchronous) and clears them if `clear`. */
+ * up (the kernel then returns early; its output is incomplete, and for the
+ * tcgen05 contraction every output of that launch is invalid).  The bits
+ * stay set until cleared, so the outputs of every asynchronous call since
+ * they were last clear are suspect.  Reads the bits of the current device
+ * (synchronous) and clears them if `clear`. */
 #define PIR_FAULT_WAIT_TIMEOUT 1u
 int pir_device_status(uint32_t* flags, int clear);
+
+/* Device memory of the library's staging pool on the current device (the
+ * stream-ordered pool the host-buffer entry points stage keys, shares and
+ * expand-and-scan scratch in): bytes it holds from the driver and bytes in
+ * use by allocations not yet freed.  Creates the pool (no memory) if the
+ * device has none yet.  Errors: PIR_ERR_ARG, PIR_ERR_CUDA. */
+int pir_staging_stats(uint64_t* reserved_bytes, uint64_t* used_bytes);
 
 /* Diagnostic of the bounded waits on the current device: runs a one-thread
  * kernel that waits on an mbarrier nothing ever completes, for at most

@@ -137,6 +137,7 @@ def _load():
         "pir_plan_inspect": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_uint32,
                                             ctypes.POINTER(pir_plan)]),
         "pir_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
+        "pir_staging_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "pir_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "pir_last_cuda_error": (ctypes.c_char_p, []),
     }
@@ -382,6 +383,13 @@ def pir_device_status(clear: bool = False) -> int:
     flags = ctypes.c_uint32(0)
     _check(_lib.pir_device_status(ctypes.byref(flags), int(clear)), "pir_device_status")
     return flags.value
+
+
+def pir_staging_stats():
+    """(reserved, used) bytes of the library's staging pool on the current device."""
+    reserved, used = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.pir_staging_stats(ctypes.byref(reserved), ctypes.byref(used)), "pir_staging_stats")
+    return int(reserved.value), int(used.value)
 
 
 def pir_multi_plan_inspect(tables, table_of_key, item_log2: int = 0):

@@ -164,45 +164,63 @@ static int eval_two_pass(const pir_table* t, uint32_t n, const uint8_t* dkeys, s
     return rc;
 }
 
-static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
-                       uint32_t* dout, uint32_t* dstatus, const pir_plan* plan_in, void* stream) {
-    if (!table_ok(shard) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+// The strategy and launch shape an evaluation of rows [row_lo, row_lo +
+// shard->rows) of a 2^n-leaf domain runs: an explicit plan (checked), else the
+// autotuned one for the shape, else the heuristic (expand + scan for one or two
+// queries on wide rows, the fused kernel otherwise).  No device work.
+static int resolve_plan(const pir_table* shard, uint64_t row_lo, uint32_t n, size_t batch, const pir_plan* plan_in,
+                        pir_plan* out) {
+    if (!table_ok(shard) || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
     if (n == 0 || n > PIR_MAX_DOMAIN_BITS) return PIR_ERR_DOMAIN;
     if (row_lo + shard->rows > (1ull << n)) return PIR_ERR_DOMAIN;
     const bool v = vec_ok(shard);
     // the scan engine's layout (its scratch is 16-byte aligned with ld % 4 == 0)
     const bool two_ok = row_lo == 0 && v && shard->stride <= 1024;
     pir_plan plan{};
-    bool have = false;
     if (plan_in) {
         plan = *plan_in;
-        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN) {
-            if (!two_ok) return PIR_ERR_UNSUPPORTED;
-            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
-        }
         int rc = PIR_ERR_ARG;
-        if (plan.strategy == PIR_STRATEGY_FUSED)
+        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN)
+            rc = two_ok ? PIR_OK : PIR_ERR_UNSUPPORTED;
+        else if (plan.strategy == PIR_STRATEGY_FUSED)
             rc = plan_check(plan, n, shard->width, v);
         else if (plan.strategy == PIR_STRATEGY_FUSED_STAGED)
             rc = plan_check_staged(plan, n, shard->width, shard->stride, v);
         if (rc != PIR_OK) return rc;
-        have = true;
-    } else if (row_lo == 0 && tuned_plan(shard->rows, shard->width, batch, v, &plan)) {
-        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN && two_ok)
-            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
+        *out = plan;
+        return PIR_OK;
+    }
+    if (row_lo == 0 && tuned_plan(shard->rows, shard->width, batch, v, &plan)) {
+        if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN && two_ok) {
+            *out = plan;
+            return PIR_OK;
+        }
         // tuned per power-of-two batch bucket: cut the last round for this batch
         plan.tail_log2 = plan_tail_log2(0, shard->rows, n, plan.group, (uint32_t)batch, plan.range_log2);
-        have = (plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK) ||
-               (plan.strategy == PIR_STRATEGY_FUSED_STAGED &&
-                plan_check_staged(plan, n, shard->width, shard->stride, v) == PIR_OK);
+        if ((plan.strategy == PIR_STRATEGY_FUSED && plan_check(plan, n, shard->width, v) == PIR_OK) ||
+            (plan.strategy == PIR_STRATEGY_FUSED_STAGED &&
+             plan_check_staged(plan, n, shard->width, shard->stride, v) == PIR_OK)) {
+            *out = plan;
+            return PIR_OK;
+        }
     }
-    if (!have) {
-        if (two_ok && two_pass_preferred(shard->rows, shard->width, batch))
-            return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
-        int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
-        if (rc != PIR_OK) return rc;
-    }
+    const int rc = plan_fused(shard->rows, row_lo, n, shard->width, (uint32_t)batch, v, &plan);
+    if (rc != PIR_OK) return rc;
+    if (two_ok && two_pass_preferred(shard->rows, shard->width, batch)) plan.strategy = PIR_STRATEGY_EXPAND_SCAN;
+    *out = plan;
+    return PIR_OK;
+}
+
+// Whether a strategy's kernels have bounded waits (mbarrier pipelines) that
+// can give up and record PIR_FAULT_WAIT_TIMEOUT in the device fault word.
+static bool strategy_waits(uint32_t strategy) {
+    return strategy == PIR_STRATEGY_EXPAND_SCAN || strategy == PIR_STRATEGY_FUSED_STAGED;
+}
+
+// Runs a resolved plan for device keys into the device output (overwritten).
+static int run_plan(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
+                    uint32_t* dout, uint32_t* dstatus, const pir_plan& plan, void* stream) {
+    if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN) return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(dout, 0, batch * shard->width * sizeof(uint32_t), s), "memset shares");
     EvalRequest req{};
@@ -218,6 +236,27 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     req.dstatus = dstatus;
     NvtxRange range("pir: fused launch");
     return launch_fused(req, plan, stream);
+}
+
+static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
+                       uint32_t* dout, uint32_t* dstatus, const pir_plan* plan_in, void* stream) {
+    if (!table_ok(shard) || !dkeys || !dout || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dkeys) & 15u) != 0) return PIR_ERR_ARG;
+    pir_plan plan{};
+    const int rc = resolve_plan(shard, row_lo, n, batch, plan_in, &plan);
+    if (rc != PIR_OK) return rc;
+    return run_plan(shard, row_lo, n, dkeys, batch, dout, dstatus, plan, stream);
+}
+
+// Two words of pinned host memory per host thread, for stream-ordered
+// snapshots of the device fault word (allocated on first use).
+static uint32_t* fault_snapshots() {
+    thread_local uint32_t* words = nullptr;
+    if (!words && cudaHostAlloc((void**)&words, 2 * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        words = nullptr;
+    }
+    return words;
 }
 
 }  // namespace pir
@@ -463,6 +502,20 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
     return launch_materialise(req, plan, dshares, ld, stream);
 }
 
+int pir_staging_stats(uint64_t* reserved_bytes, uint64_t* used_bytes) {
+    using namespace pir;
+    if (!reserved_bytes || !used_bytes) return PIR_ERR_ARG;
+    cudaMemPool_t pool = nullptr;
+    const int rc = staging_pool(&pool);
+    if (rc != PIR_OK) return rc;
+    uint64_t reserved = 0, used = 0;
+    CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved), "staging pool reserved");
+    CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used), "staging pool used");
+    *reserved_bytes = reserved;
+    *used_bytes = used;
+    return PIR_OK;
+}
+
 int pir_selftest_bounded_wait(uint32_t polls, void* stream) {
     if (polls == 0) return PIR_ERR_ARG;
     return pir::selftest_bounded_wait(polls, stream);
@@ -515,9 +568,24 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
     } else {
         dout = out;
     }
+    // a strategy whose kernels have bounded waits: snapshot the device fault
+    // word before and after it (stream-ordered), so that a wait that gave up
+    // during this call turns into PIR_ERR_TIMEOUT once the call synchronizes
+    pir_plan plan{};
+    rc = resolve_plan(t, 0, n, batch, nullptr, &plan);
+    uint32_t* snap = !out_on_device && rc == PIR_OK && strategy_waits(plan.strategy) ? fault_snapshots() : nullptr;
+    uint32_t* fault_word = snap ? device_fault_word() : nullptr;
     cudaError_t e = cudaMemcpyAsync(dkeys, keys, batch * kb, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) rc = cuda_fail((int)e, "copy keys");
-    if (rc == PIR_OK) rc = eval_device(t, 0, n, dkeys, batch, dout, nullptr, nullptr, stream);
+    if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "copy keys");
+    if (rc == PIR_OK && fault_word) {
+        e = cudaMemcpyAsync(&snap[0], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
+    }
+    if (rc == PIR_OK) rc = run_plan(t, 0, n, dkeys, batch, dout, nullptr, plan, stream);
+    if (rc == PIR_OK && fault_word) {
+        e = cudaMemcpyAsync(&snap[1], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
+    }
     if (rc == PIR_OK && !out_on_device) {
         e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "copy shares");
@@ -527,6 +595,7 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
     if (!out_on_device) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
+        if (rc == PIR_OK && fault_word && (snap[1] & ~snap[0] & PIR_FAULT_WAIT_TIMEOUT)) rc = PIR_ERR_TIMEOUT;
     }
     return rc;
 }

@@ -14,9 +14,13 @@
 // the array's name is only a host-side stand-in, so its device address is
 // looked up with cudaGetSymbolAddress once per device (with that device
 // current) on the first call made on that device, and passed to the kernel.
+// A device whose primary context is destroyed and created again
+// (cudaDeviceReset) gets the array at a new address: the lookup is kept with
+// the context's unique ID and repeated when the current context's ID differs.
 // All calls share the region and it keeps the last call's contents: the
 // share area is cleared at the start of every call, and calls whose work
 // overlaps on the GPU (concurrent streams, or other host threads) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,19 +39,48 @@ static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
 uint8_t* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // unique ID of the context the address belongs to
 
-// Device address of g_scratch on the current device (looked up on first use).
+// The driver's current context and its unique ID, through the runtime's
+// driver entry points (the library does not link the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    return get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_scratch on the current device: looked up on the first
+// call on the device, and again once its context has been replaced.
 int scratch_for_current_device(uint8_t** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail((int)e, "noalloc: current device");
     if (dev < 0 || dev >= kMaxDevices) return PIR_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx);
+    if (!g_scratch_ptr[dev] || !have_ctx || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);  // makes the device's primary context current
         if (e != cudaSuccess) return cuda_fail((int)e, "noalloc: scratch address");
         g_scratch_ptr[dev] = static_cast<uint8_t*>(p);
+        g_scratch_ctx[dev] = current_context_id(&ctx) ? ctx : 0;
     }
     *out = g_scratch_ptr[dev];
     return PIR_OK;
@@ -62,6 +95,13 @@ extern "C" int pir_server_eval_noalloc(const pir_table* t, const uint8_t* keys, 
     if (!t || !t->data || !keys || !out || batch == 0 || t->rows < 1 || t->width < 1 || t->stride < t->width ||
         (reinterpret_cast<uintptr_t>(t->data) & 3u) != 0)
         return PIR_ERR_ARG;
+    {  // `out` is written by a device-to-host copy: it must be host memory
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, out) != cudaSuccess)
+            cudaGetLastError();  // unregistered host memory on older runtimes
+        else if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+            return PIR_ERR_ARG;
+    }
     const uint32_t n = pir_domain_bits(t->rows);
     if (n == 0) return PIR_ERR_DOMAIN;
     const size_t kb = key_bytes(n);

@@ -86,3 +86,28 @@ def test_cancel_withdraws_pending_requests(env):
             assert np.array_equal(rec.astype(np.uint32), table[alphas[i]].cpu().numpy().view(np.uint32))
     assert srv.stats()["cancelled"] == n_cancelled
     srv.close()
+
+
+def test_host_call_reports_only_timeouts_of_its_own_kernels(env):
+    """pir_server_eval with a host `out` snapshots the device fault word around
+    kernels with bounded waits (here the expand-and-scan strategy of one query
+    on 128 MiB of 64-word rows) and returns PIR_ERR_TIMEOUT only for a bit
+    that one of them set: a bit left set by an earlier launch (the bounded-wait
+    diagnostic) is not this call's, and the call returns the exact shares."""
+    torch, pir, orc = env
+    rows, W = 1 << 19, 64
+    assert pir.pir_plan_for(rows, W, 1).strategy == pir.PIR_STRATEGY_EXPAND_SCAN
+    table = wl.table_u32_torch(63, rows, W, "cuda")
+    n = pir.pir_domain_bits(rows)
+    ks0, ks1 = make_keys(orc, n, [rows - 7], [1], 63)
+    pir.pir_device_status(clear=True)
+    assert pir.pir_selftest_bounded_wait(4096) == -6  # leaves PIR_FAULT_WAIT_TIMEOUT set
+    shares = []
+    for k in (ks0[0], ks1[0]):
+        out = np.zeros((1, W), np.uint32)
+        pir.pir_server_eval(table, k, 1, out)  # raises on PIR_ERR_TIMEOUT
+        shares.append(out[0])
+    assert pir.pir_device_status(clear=True) & pir.PIR_FAULT_WAIT_TIMEOUT  # still set, not cleared by the call
+    T = table.cpu().numpy().view(np.uint32)
+    assert np.array_equal(shares[0], orc.answer(ks0[0], T))
+    assert np.array_equal(pir.pir_reconstruct(shares[0], shares[1]), T[rows - 7])

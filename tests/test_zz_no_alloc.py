@@ -70,3 +70,36 @@ def test_noalloc_rejects_batches_beyond_its_region(env):
     with pytest.raises(pir.PirError) as e:
         pir.pir_server_eval_noalloc(table, keys, too_many, out)
     assert e.value.code == -8
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """After one warm-up call (the region's one-time address lookup), calls of
+    several shapes leave the device's free memory and the library's staging
+    pool (reserved and in-use bytes) exactly as they were."""
+    torch, pir = env
+    cases = [_case(torch, pir, rows, width, batch, seed)
+             for rows, width, batch, seed in ((5000, 16, 7, 4), (1 << 12, 64, 3, 5), (1 << 14, 8, 20, 6))]
+    T, table, alphas, pairs = cases[0]
+    out = np.zeros((len(pairs), T.shape[1]), np.uint32)
+    pir.pir_server_eval_noalloc(table, b"".join(p[0] for p in pairs), len(pairs), out)
+    torch.cuda.synchronize()
+    free0, pool0 = torch.cuda.mem_get_info()[0], pir.pir_staging_stats()
+    for _ in range(3):
+        for T, table, alphas, pairs in cases:
+            got = np.zeros((len(pairs), T.shape[1]), np.uint32)
+            pir.pir_server_eval_noalloc(table, b"".join(p[0] for p in pairs), len(pairs), got)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert pir.pir_staging_stats() == pool0
+
+
+def test_noalloc_refuses_a_device_output(env):
+    """The shares are copied back to host memory: a device `out` is an
+    argument error, not a copy into device memory."""
+    torch, pir = env
+    T, table, _, pairs = _case(torch, pir, 5000, 16, 2, 7)
+    dout = torch.zeros((2, 16), dtype=torch.int32, device="cuda")
+    with pytest.raises(pir.PirError) as e:
+        pir.pir_server_eval_noalloc(table, b"".join(p[0] for p in pairs), 2, dout)
+    assert e.value.code == -1
+    assert not dout.any()
