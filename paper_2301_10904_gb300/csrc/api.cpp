@@ -1,6 +1,7 @@
 // C-ABI server entry points: argument checks, buffer staging, dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -217,12 +218,13 @@ static bool strategy_waits(uint32_t strategy) {
     return strategy == PIR_STRATEGY_EXPAND_SCAN || strategy == PIR_STRATEGY_FUSED_STAGED;
 }
 
-// Runs a resolved plan for device keys into the device output (overwritten).
+// Runs a resolved plan for device keys into the device output (overwritten;
+// `zeroed`: the caller knows it already holds zeros).
 static int run_plan(const pir_table* shard, uint64_t row_lo, uint32_t n, const uint8_t* dkeys, size_t batch,
-                    uint32_t* dout, uint32_t* dstatus, const pir_plan& plan, void* stream) {
+                    uint32_t* dout, uint32_t* dstatus, const pir_plan& plan, void* stream, bool zeroed = false) {
     if (plan.strategy == PIR_STRATEGY_EXPAND_SCAN) return eval_two_pass(shard, n, dkeys, batch, dout, dstatus, stream);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemsetAsync(dout, 0, batch * shard->width * sizeof(uint32_t), s), "memset shares");
+    if (!zeroed) CUDA_TRY(cudaMemsetAsync(dout, 0, batch * shard->width * sizeof(uint32_t), s), "memset shares");
     EvalRequest req{};
     req.table = shard->data;
     req.row_lo = row_lo;
@@ -246,6 +248,44 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     const int rc = resolve_plan(shard, row_lo, n, batch, plan_in, &plan);
     if (rc != PIR_OK) return rc;
     return run_plan(shard, row_lo, n, dkeys, batch, dout, dstatus, plan, stream);
+}
+
+// Device staging of the synchronous host-buffer path, per host thread and
+// device: keys and shares of a small call (a lone query, the latency-bound
+// case) without a stream-ordered allocation and free per call.  A call
+// returns only after its shares are back on the host, so the next call of
+// the same thread finds the buffer idle; the share area is cleared after the
+// copy back (stream-ordered, off the next call's critical path) and `cleared`
+// orders that clearing before the next call's kernel on whatever stream it
+// uses.  `zero_bytes`: how much of the share area, from its start, holds
+// zeros (a call writes only the first batch x width words).  Kept until the
+// thread exits.
+constexpr size_t kStageKeyBytes = 32u << 10, kStageShareBytes = 32u << 10;
+struct HostStage {
+    uint8_t* keys = nullptr;  // kStageKeyBytes, then kStageShareBytes of shares
+    cudaEvent_t copied = nullptr, cleared = nullptr;
+    size_t zero_bytes = 0;
+    ~HostStage() {
+        if (copied) cudaEventDestroy(copied);
+        if (cleared) cudaEventDestroy(cleared);
+        if (keys) cudaFree(keys);
+    }
+};
+static HostStage* host_stage() {
+    thread_local HostStage stages[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    HostStage& st = stages[dev];
+    if (!st.keys) {
+        if (cudaMalloc((void**)&st.keys, kStageKeyBytes + kStageShareBytes) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st.copied, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st.cleared, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;  // the caller falls back to the pool
+        }
+        st.zero_bytes = 0;
+    }
+    return &st;
 }
 
 // Two words of pinned host memory per host thread, for stream-ordered
@@ -553,35 +593,49 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool out_on_device = is_device_pointer(out);
     const size_t out_bytes = batch * (size_t)t->width * sizeof(uint32_t);
-    uint8_t* dkeys = nullptr;
-    uint32_t* dout = nullptr;
-    cudaMemPool_t pool = nullptr;
-    int rc = staging_pool(&pool);
+    pir_plan plan{};
+    int rc = resolve_plan(t, 0, n, batch, nullptr, &plan);
     if (rc != PIR_OK) return rc;
-    CUDA_TRY(cudaMallocFromPoolAsync((void**)&dkeys, batch * kb, pool, s), "alloc keys");
-    if (!out_on_device) {
-        cudaError_t e = cudaMallocFromPoolAsync((void**)&dout, out_bytes, pool, s);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(dkeys, s);
-            return cuda_fail((int)e, "alloc shares");
-        }
-    } else {
-        dout = out;
-    }
     // a strategy whose kernels have bounded waits: snapshot the device fault
     // word before and after it (stream-ordered), so that a wait that gave up
     // during this call turns into PIR_ERR_TIMEOUT once the call synchronizes
-    pir_plan plan{};
-    rc = resolve_plan(t, 0, n, batch, nullptr, &plan);
-    uint32_t* snap = !out_on_device && rc == PIR_OK && strategy_waits(plan.strategy) ? fault_snapshots() : nullptr;
+    uint32_t* snap = !out_on_device && strategy_waits(plan.strategy) ? fault_snapshots() : nullptr;
     uint32_t* fault_word = snap ? device_fault_word() : nullptr;
-    cudaError_t e = cudaMemcpyAsync(dkeys, keys, batch * kb, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "copy keys");
+    HostStage* st = !out_on_device && batch * kb <= kStageKeyBytes && out_bytes <= kStageShareBytes &&
+                            plan.strategy != PIR_STRATEGY_EXPAND_SCAN
+                        ? host_stage()
+                        : nullptr;
+    uint8_t* dkeys = nullptr;
+    uint32_t* dout = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (st) {
+        dkeys = st->keys;
+        dout = reinterpret_cast<uint32_t*>(st->keys + kStageKeyBytes);
+        if (st->zero_bytes) CUDA_TRY(cudaStreamWaitEvent(s, st->cleared, 0), "wait staging cleared");
+    } else {
+        rc = staging_pool(&pool);
+        if (rc != PIR_OK) return rc;
+        CUDA_TRY(cudaMallocFromPoolAsync((void**)&dkeys, batch * kb, pool, s), "alloc keys");
+        if (!out_on_device) {
+            e = cudaMallocFromPoolAsync((void**)&dout, out_bytes, pool, s);
+            if (e != cudaSuccess) {
+                cudaFreeAsync(dkeys, s);
+                return cuda_fail((int)e, "alloc shares");
+            }
+        } else {
+            dout = out;
+        }
+    }
+    e = cudaMemcpyAsync(dkeys, keys, batch * kb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail((int)e, "copy keys");
     if (rc == PIR_OK && fault_word) {
         e = cudaMemcpyAsync(&snap[0], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
     }
-    if (rc == PIR_OK) rc = run_plan(t, 0, n, dkeys, batch, dout, nullptr, plan, stream);
+    const size_t zero_before = st ? st->zero_bytes : 0;
+    if (rc == PIR_OK) rc = run_plan(t, 0, n, dkeys, batch, dout, nullptr, plan, stream, st && out_bytes <= zero_before);
+    if (st) st->zero_bytes = 0;
     if (rc == PIR_OK && fault_word) {
         e = cudaMemcpyAsync(&snap[1], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
@@ -590,13 +644,25 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
         e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "copy shares");
     }
-    if (!out_on_device) cudaFreeAsync(dout, s);
-    cudaFreeAsync(dkeys, s);
-    if (!out_on_device) {
-        e = cudaStreamSynchronize(s);
+    if (st) {
+        // the shares are on their way back: clear the share area for the next
+        // call behind them, and wait for the copy alone
+        if (rc == PIR_OK) e = cudaEventRecord(st->copied, s);
+        if (rc == PIR_OK && e == cudaSuccess) e = cudaMemsetAsync(dout, 0, out_bytes, s);
+        if (rc == PIR_OK && e == cudaSuccess) e = cudaEventRecord(st->cleared, s);
+        if (rc == PIR_OK && e == cudaSuccess) st->zero_bytes = std::max(out_bytes, zero_before);
+        if (rc == PIR_OK && e != cudaSuccess) rc = cuda_fail((int)e, "staging clear");
+        e = rc == PIR_OK ? cudaEventSynchronize(st->copied) : cudaStreamSynchronize(s);
         if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
-        if (rc == PIR_OK && fault_word && (snap[1] & ~snap[0] & PIR_FAULT_WAIT_TIMEOUT)) rc = PIR_ERR_TIMEOUT;
+    } else {
+        if (!out_on_device) cudaFreeAsync(dout, s);
+        cudaFreeAsync(dkeys, s);
+        if (!out_on_device) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
+        }
     }
+    if (rc == PIR_OK && fault_word && (snap[1] & ~snap[0] & PIR_FAULT_WAIT_TIMEOUT)) rc = PIR_ERR_TIMEOUT;
     return rc;
 }
 

@@ -39,8 +39,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "async_copy.cuh"
 #include "internal.h"
@@ -1327,13 +1331,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1) multi_eval_kernel(const Mult
     }
 }
 
+// Sets a kernel's dynamic shared memory limit once per device (the attribute
+// is per function and device; setting it costs ~1 us, a launch-path cost worth
+// avoiding for latency-bound single queries).  Thread-safe: setting it twice
+// is harmless.
+// A device reset drops the attribute: a launch refused after the attribute
+// was recorded as set sets it again (force) and retries once (a refused launch
+// enqueues nothing).
+template <typename Kern>
+cudaError_t smem_attribute_once(Kern kern, int bytes, bool force = false) {
+    static std::atomic<uint64_t> done{0};  // one bit per device, per kernel
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (!force && bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 template <typename Kern>
 cudaError_t launch_kernel(Kern kern, const FusedParams& p, uint32_t ctas, int threads, cudaStream_t s) {
-    // the attribute is per function and device; setting it each launch costs ~1 us and is always correct
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = smem_attribute_once(kern, kSmemBytes);
     if (e != cudaSuccess) return e;
     kern<<<ctas, threads, kSmemBytes, s>>>(p);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaErrorInvalidValue) {
+        e = smem_attribute_once(kern, kSmemBytes, true);
+        if (e != cudaSuccess) return e;
+        kern<<<ctas, threads, kSmemBytes, s>>>(p);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace dev
@@ -1355,9 +1385,12 @@ static bool reserved_smem_ok() {
 }
 
 int device_sm_count() {
+    static std::atomic<int> cached[64] = {};  // per device; the SM count of a device never changes
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && (sms = cached[dev].load(std::memory_order_relaxed)) > 0) return sms;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64) cached[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 
@@ -1468,9 +1501,30 @@ int plan_check(const pir_plan& plan, uint32_t n, uint32_t width, bool vec_ok) {
     return PIR_OK;
 }
 
+// The planner is a pure function of its arguments; evaluations of one shape
+// on the latency-bound path (a lone query per call) reuse its answer.
 int plan_fused(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok,
                pir_plan* plan) {
-    return plan_fused_sms(rows, row_lo, n, width, batch, vec_ok, std::max(1, device_sm_count()), plan);
+    using Key = std::tuple<int, uint64_t, uint64_t, uint32_t, uint32_t, uint32_t, bool>;
+    static std::mutex mu;
+    static std::map<Key, pir_plan> memo;
+    const int sms = std::max(1, device_sm_count());
+    const Key key{sms, rows, row_lo, n, width, batch, vec_ok};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) {
+            *plan = it->second;
+            return PIR_OK;
+        }
+    }
+    const int rc = plan_fused_sms(rows, row_lo, n, width, batch, vec_ok, sms, plan);
+    if (rc == PIR_OK) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (memo.size() >= 4096) memo.clear();
+        memo.emplace(key, *plan);
+    }
+    return rc;
 }
 
 int plan_fused_sms(uint64_t rows, uint64_t row_lo, uint32_t n, uint32_t width, uint32_t batch, bool vec_ok, int sms,
@@ -1559,12 +1613,16 @@ int launch_multi(const MultiParams& mp, bool vec, void* stream) {
     const uint32_t ctas = grid_for(mp.nitems);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     auto kern = vec ? dev::multi_eval_kernel<4> : dev::multi_eval_kernel<1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kSmemBytes);
-    if (e == cudaSuccess) {
+    for (int attempt = 0; attempt < 2; ++attempt) {  // the second sets the attribute again (after a reset)
+        cudaError_t e = vec ? dev::smem_attribute_once(dev::multi_eval_kernel<4>, dev::kSmemBytes, attempt > 0)
+                            : dev::smem_attribute_once(dev::multi_eval_kernel<1>, dev::kSmemBytes, attempt > 0);
+        if (e != cudaSuccess) return cuda_fail((int)e, "multi_eval attribute");
         kern<<<ctas, dev::kFusedThreads, dev::kSmemBytes, s>>>(mp);
         e = cudaGetLastError();
+        if (e == cudaSuccess) return PIR_OK;
+        if (e != cudaErrorInvalidValue || attempt > 0) return cuda_fail((int)e, "multi_eval launch");
     }
-    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "multi_eval launch");
+    return PIR_OK;
 }
 
 // Partial batch retrieval: `batch` bins of bin_rows rows (the last clipped to

@@ -325,3 +325,22 @@ def test_library_keys_on_gpu_reconstruct(env):
     g1 = run_device(torch, pir, table, [p[1] for p in pairs], width)
     for q in range(batch):
         assert np.array_equal(pir.pir_reconstruct(g0[q], g1[q]), T[alphas[q]])
+
+
+def test_host_entry_point_repeated_calls_and_streams(env):
+    """Small synchronous calls reuse one staging buffer per host thread and
+    device, whose share area is cleared after each call's copy back: calls of
+    growing and shrinking widths and batches, on two streams in turn, each
+    match the oracle word for word (stale or partly cleared staging would
+    show up here)."""
+    torch, pir, orc = env
+    streams = [torch.cuda.Stream(), torch.cuda.current_stream()]
+    cases = [(3000, 8, 1), (3000, 64, 3), (5000, 16, 7), (3000, 8, 2), (1 << 12, 128, 4), (5000, 16, 1)]
+    for i, (rows, width, batch) in enumerate(cases * 2):
+        n = pir.pir_domain_bits(rows)
+        T = wl.table_u32(rows + width, rows, width)
+        ks0, _ = make_keys(orc, n, wl.alphas(i, rows, batch), [1] * batch, 90 + i)
+        out = np.full((batch, width), 0x5A5A5A5A, np.uint32)
+        pir.pir_server_eval(dev_table(torch, T), b"".join(ks0), batch, out, stream=streams[i % 2])
+        for q in range(batch):
+            assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, q)
