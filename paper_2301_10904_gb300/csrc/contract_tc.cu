@@ -21,9 +21,9 @@
 //    tile (64 x TN u32), split them into fp16 limb planes and store the
 //    planes in shared memory in the 128-byte-swizzled K-major layout the
 //    tensor core reads; two stages with full/empty mbarriers;
-//  - one lane of warp 4 issues a stage's 40 tcgen05.mma (M = 128, N = TN,
-//    K = 16; A = a limb plane of S, B = a limb plane of T) into the class
-//    accumulators and frees the stage with tcgen05.commit;
+//  - one lane of warp 4 issues a stage's 16 tcgen05.mma (M = 128, K = 16;
+//    A = limb plane i of S, B = limb planes 0..3-i of T side by side, N =
+//    (4 - i) TN, into classes i..3) and frees the stage with tcgen05.commit;
 //  - warps 0-3 (TMEM lanes 0-127, one per query row of the tile) drain one
 //    accumulator set with tcgen05.ld while the MMAs fill the other.
 // Split-k partial tiles meet in out with u32 atomics (order-independent, so
@@ -67,10 +67,12 @@ struct TcShape {
     static constexpr uint32_t kStageBytes = 4 * kTcPlaneA + 4 * kPlaneB;
     static constexpr uint32_t kSmem = 1024 /* alignment slack */ + kTcHeader + kTcStages * kStageBytes;
     static constexpr uint32_t kTmemCols = 2 * 4 * TN;  // two accumulator sets of four classes
-    // instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B f16
-    // (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits
-    // 17-22, M >> 4 at bits 24-28
-    static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((kTcM >> 4) << 24);
+    // instruction descriptor of kind::f16 for an MMA of N = nplanes * TN: D f32
+    // (bits 4-5 = 1), A and B f16 (bits 7-9, 10-12 = 0), both K-major (bits 15,
+    // 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    __host__ __device__ static constexpr uint32_t idesc(uint32_t nplanes) {
+        return (1u << 4) | ((nplanes * (uint32_t)TN >> 3) << 17) | ((kTcM >> 4) << 24);
+    }
     static_assert(kSmem <= 227u * 1024u, "shared memory");
     static_assert(kTmemCols >= 32 && kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
     static_assert(kPlaneB % 1024 == 0 && kTcPlaneA % 1024 == 0 && kTcHeader % 1024 == 0, "swizzle atoms");
@@ -316,13 +318,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
             mbar_arrive(base + kTcFull + 8u * s);
             return true;
         };
-        // a stage's loads are in flight while the warp waits for a free
-        // shared-memory stage (the MMAs of two stages back)
-        for (uint32_t g = 0; g < nst; ++g) {
+        if constexpr (TN == 64) {
+            // Two stages' loads in flight: stage g + 1's are issued before stage
+            // g is converted (and before the wait for a free shared-memory
+            // stage, the MMAs of two stages back).  (Measured: 0.414 -> 0.403 ms
+            // at 256 x 2^20 x 64; slower with 32-word tiles, which keep one.)
             uint4 a[8], t[4];
-            load_a(g, a);
-            load_t(g, t);
-            if (!convert_stage(g, a, t)) break;
+            if (nst) {
+                load_a(0, a);
+                load_t(0, t);
+            }
+            for (uint32_t g = 0; g < nst; ++g) {
+                uint4 an[8], tn[4];
+                if (g + 1 < nst) {
+                    load_a(g + 1, an);
+                    load_t(g + 1, tn);
+                }
+                if (!convert_stage(g, a, t)) break;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = an[i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t[i] = tn[i];
+            }
+        } else {
+            // a stage's loads are in flight while the warp waits for a free
+            // shared-memory stage (the MMAs of two stages back)
+            for (uint32_t g = 0; g < nst; ++g) {
+                uint4 a[8], t[4];
+                load_a(g, a);
+                load_t(g, t);
+                if (!convert_stage(g, a, t)) break;
+            }
         }
     } else if (warp == kTcMmaWarp) {
         // ---- MMA issue: 4 k-steps x 10 limb pairs per stage ------------------
@@ -336,18 +362,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(const TcPara
                 if (!wait_bounded(base + kTcFull + 8u * s, (g >> 1) & 1u, abort_flag, p.faults)) break;
                 tc_fence_after();
                 const uint32_t stage = base + kTcHeader + s * Sh::kStageBytes;
+                // Limb plane i of S times limb planes 0..3-i of T lands in classes
+                // i..3: the T planes lie back to back in the stage (N = TN per
+                // plane) and the classes side by side in tensor memory, so one
+                // MMA of N = (4 - i) TN does all of them (4 MMAs per k-step).
+                const uint64_t bd0 = sw128_desc(stage + 4u * kTcPlaneA);
 #pragma unroll
                 for (uint32_t t = 0; t < kTcStageK / 16; ++t) {
 #pragma unroll
                     for (uint32_t i = 0; i < 4; ++i) {
                         const uint64_t ad = sw128_desc(stage + i * kTcPlaneA) + 2u * t;  // + 32 bytes per k-step
-#pragma unroll
-                        for (uint32_t j = 0; i + j < 4; ++j) {
-                            const uint64_t bd = sw128_desc(stage + 4u * kTcPlaneA + j * Sh::kPlaneB) + 2u * t;
-                            // class i + j; its first MMA of a chunk (i = 0, first k-step) overwrites
-                            mma_f16(tmem + (b * 4u + i + j) * (uint32_t)TN, ad, bd, Sh::kIdesc,
-                                    (first && t == 0 && i == 0) ? 0u : 1u);
-                        }
+                        // the chunk's first MMA (i = 0, first k-step) overwrites every class
+                        mma_f16(tmem + (b * 4u + i) * (uint32_t)TN, ad, bd0 + 2u * t, Sh::idesc(4u - i),
+                                (first && t == 0 && i == 0) ? 0u : 1u);
                     }
                 }
                 mma_commit(base + kTcEmpty + 8u * s);
