@@ -956,8 +956,9 @@ class PbrWorkload:
         self.nodes_per_step = self.nbins * ((1 << self.nb) - 1)
         # a step is two launches (the expansion into scratch, then the diagonal scan); the roofline
         # is the expansion's, its kernel timed alone through pir_expand_materialise (the same kernel
-        # and launch shape as inside the step), see dominant_kernel()
-        self.kernel = "expand_materialise_kernel"
+        # and launch shape as inside the step: every bin's tree breadth first, several bins per CTA),
+        # see dominant_kernel()
+        self.kernel = "expand_bfs_kernel"
         self.launches_per_step = 2
         self.scratch = torch.empty((self.nbins, self.bin_rows), dtype=torch.int32, device=device)
         self.h2d_bytes, self.d2h_bytes = len(k0), self.nbins * self.width * 4

@@ -1287,6 +1287,153 @@ __global__ void __launch_bounds__(kProducers, 1) expand_materialise_kernel(const
     eval_items<G, 1, true, false>(p);
 }
 
+// ------------------------------------------------ many small trees, breadth first
+// Expansion only, for a batch of keys over a small domain (the bins of
+// partial batch retrieval).  Each key's tree is cut into 2^u units, the
+// subtrees at depth u; CTA c takes units [c*upc, c*upc + upc), walks each
+// unit's root down from its key's root (u levels, one block each) and then
+// expands all its units together, level by level, over its 512 threads.  The
+// nodes of a level lie unit-major in shared memory after the lookup tables
+// (node i = unit * 2^l + j, children 2i and 2i + 1), in one of two buffers by
+// the level's parity; the leaf parents write the leaf shares straight to
+// shares[key * ld + leaf].  With the units spread evenly over every SM and
+// each level's nodes over every thread, no work item leaves threads or SMs
+// idle, as G-query items on a small tree do (1024 bins of 2^10 rows make 128
+// such items for 152 SMs; as 4096 units of 2^8 leaves they make 27 per SM).
+constexpr int kBfsOff = kTablesBytes;
+constexpr int kBfsLastBytes = 64 * 1024;   // the leaf parents' level: up to 4096 nodes
+constexpr int kBfsOtherBytes = 32 * 1024;  // the level above it: up to 2048 nodes
+constexpr int kBfsHdrOff = kBfsOff + kBfsLastBytes + kBfsOtherBytes;
+constexpr uint32_t kBfsMaxUnits = 64;      // units per CTA (one 16-byte header each)
+constexpr uint32_t kBfsMaxLeaves = 2u * kBfsLastBytes / 16u;  // leaves per CTA
+constexpr int kBfsSmemBytes = kBfsHdrOff + 16 * (int)kBfsMaxUnits;
+static_assert(kBfsSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
+static_assert(kBfsMaxLeaves / 4u * 16u <= (uint32_t)kBfsOtherBytes, "the level above the leaf parents fits");
+
+struct BfsParams {
+    const uint8_t* keys;
+    uint32_t key_bytes;
+    uint32_t n;      // tree levels of every key
+    uint32_t u;      // unit depth: 2^u units per key, 0 <= u < n
+    uint32_t nunits; // keys << u
+    uint32_t upc;    // units per CTA
+    uint32_t* shares;
+    uint64_t ld;     // shares[key * ld + j]
+    uint64_t rows;   // leaves j < rows are written
+    uint32_t vec2;   // shares 8-byte aligned and ld even: leaf pairs as one 8-byte store
+    uint32_t* status;
+};
+
+// Child b of v at depth d (1-based) of `key` in global memory: PRF plus the
+// codeword C_{lsb(v)}[b][d].
+__device__ __forceinline__ uint4 expand1(uint32_t lane4, uint32_t lane4h, const uint8_t* key, uint32_t d, uint4 v,
+                                         uint32_t b, bool chacha) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(key + PIR_KEY_HEADER_BYTES + 64u * (d - 1) +
+                                                         32u * (v.x & 1u) + 16u * b));
+    uint4 c;
+    if (chacha) {
+        uint4 c0, c1;
+        prf2_chacha(v, c0, c1);
+        c = b ? c1 : c0;
+    } else {
+        c = prf1(lane4, lane4h, v, b);
+    }
+    return xor4(c, w);
+}
+
+__global__ void __launch_bounds__(kProducers, 1) expand_bfs_kernel(const BfsParams p) {
+    if (!smem_base_ok(p.status)) return;
+    const int tid = threadIdx.x;
+    const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
+    const uint32_t t0 = blockIdx.x * p.upc;
+    const uint32_t nt = min(p.upc, p.nunits - t0);
+    const int n = (int)p.n, u = (int)p.u, h = n - u;  // levels below a unit's root
+    uint4* hdr = reinterpret_cast<uint4*>(sm + kBfsHdrOff);  // per unit: its key's ok, party, cw_out, PRF
+    uint4* const buf_last = reinterpret_cast<uint4*>(sm + kBfsOff);
+    uint4* const buf_other = reinterpret_cast<uint4*>(sm + kBfsOff + kBfsLastBytes);
+    auto level = [&](int l) { return ((l ^ (h - 1)) & 1) ? buf_other : buf_last; };
+    auto key_of = [&](uint32_t t) { return p.keys + (uint64_t)((t0 + t) >> u) * p.key_bytes; };
+    build_tables(tid);  // ends with a CTA barrier
+
+    // ---- headers and unit roots: u levels down from the key's root ----------
+    for (uint32_t t = (uint32_t)tid; t < nt; t += kProducers) {
+        const uint4* key = reinterpret_cast<const uint4*>(key_of(t));
+        const uint4 hw = __ldg(key);
+        const uint32_t ok = hw.x == kKeyMagic && (hw.y & 0xffu) == kKeyVersion && ((hw.y >> 8) & 0xffu) == p.n &&
+                            ((hw.y >> 16) & 0xffu) <= 1u && (hw.y >> 24) <= PIR_PRF_CHACHA20;
+        if (!ok && p.status) atomicOr(p.status, PIR_STATUS_BAD_KEY);
+        hdr[t] = make_uint4(ok, (hw.y >> 16) & 1u, hw.z, hw.y >> 24);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (ok) {
+            v = __ldg(key + 1);
+            const uint32_t path = (t0 + t) & ((1u << u) - 1u);
+            for (int d = 1; d <= u; ++d)  // only the child on the path
+                v = expand1(lane4, lane4h, key_of(t), (uint32_t)d, v, (path >> (u - d)) & 1u, (hw.y >> 24) != 0);
+        }
+        level(0)[t] = v;
+    }
+    __syncthreads();
+
+    // ---- internal levels below the unit roots: level l -> l + 1 -------------
+    for (int l = 0; l + 1 < h; ++l) {
+        const uint4* src = level(l);
+        uint4* dst = level(l + 1);
+        const uint32_t cnt = nt << l;
+        const uint32_t depth = (uint32_t)(u + l + 1);  // of the children
+        if (cnt <= (uint32_t)kProducers / 2) {
+            // few nodes: a thread per child, one AES block each (the level's latency)
+            if ((uint32_t)tid < 2u * cnt) {
+                const uint32_t i = (uint32_t)tid >> 1, b = (uint32_t)tid & 1u, t = i >> l;
+                const uint4 hd = hdr[t], v = src[i];
+                dst[2u * i + b] = hd.x ? expand1(lane4, lane4h, key_of(t), depth, v, b, hd.w != 0) : v;
+            }
+        } else {
+            for (uint32_t i = (uint32_t)tid; i < cnt; i += kProducers) {
+                const uint32_t t = i >> l;
+                const uint4 hd = hdr[t], v = src[i];
+                uint4 c0 = v, c1 = v;
+                if (hd.x) expand(lane4, lane4h, key_of(t), depth, v, false, hd.w != 0, c0, c1);
+                dst[2u * i] = c0;
+                dst[2u * i + 1u] = c1;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- leaf parents -> leaf shares, y = (-1)^party (word1 + lsb * cw_out) --
+    const uint4* src = level(h - 1);
+    const uint32_t cnt = nt << (h - 1);
+    const uint32_t jmask = (1u << (h - 1)) - 1u;
+    for (uint32_t i = (uint32_t)tid; i < cnt; i += kProducers) {
+        const uint32_t t = i >> (h - 1), g = t0 + t;
+        // leaf within the key: the unit's first leaf plus this pair's offset
+        const uint64_t j = ((uint64_t)(g & ((1u << u) - 1u)) << h) + 2ull * (i & jmask);
+        const uint4 hd = hdr[t];
+        uint32_t y0 = 0, y1 = 0;
+        if (hd.x) {
+            uint4 c0, c1;
+            expand(lane4, lane4h, key_of(t), (uint32_t)n, src[i], true, hd.w != 0, c0, c1);
+            y0 = c0.y + (c0.x & 1u) * hd.z;
+            y1 = c1.y + (c1.x & 1u) * hd.z;
+            if (hd.y) {
+                y0 = 0u - y0;
+                y1 = 0u - y1;
+            }
+        }
+        uint32_t* dst = p.shares + (uint64_t)(g >> u) * p.ld + j;
+        if (j + 1 < p.rows) {
+            if (p.vec2)
+                *reinterpret_cast<uint2*>(dst) = make_uint2(y0, y1);
+            else {
+                dst[0] = y0;
+                dst[1] = y1;
+            }
+        } else if (j < p.rows) {
+            dst[0] = y0;
+        }
+    }
+}
+
 // Many tables of different sizes and widths in one launch.  Items are
 // (table, row range, up to 8 queries of that table); CTAs take the next item
 // from a counter, so uneven items balance themselves.
@@ -1579,8 +1726,59 @@ static uint32_t grid_for(uint64_t items) {
     return (uint32_t)std::min<uint64_t>(items, (uint64_t)sms);
 }
 
+// Many small trees: the batch's keys, cut into 2^u units each, spread evenly
+// over up to one CTA per SM, every CTA expanding its units breadth first
+// (expand_bfs_kernel).  PIR_ERR_UNSUPPORTED where a CTA would hold more than
+// kBfsMaxUnits units or kBfsMaxLeaves leaves for every u, or the rows do not
+// start at the domain's first leaf.
+static int launch_expand_bfs(const EvalRequest& req, uint32_t* shares, uint64_t ld, cudaStream_t s) {
+    if (req.row_lo != 0 || req.batch == 0 || req.n == 0 || req.n > 31) return PIR_ERR_UNSUPPORTED;
+    const uint64_t sms = (uint64_t)std::max(1, device_sm_count());
+    // unit depth u: the fewest leaves on the busiest CTA (ties: the smaller u,
+    // fewer path walks), within the CTA's level buffers and header slots
+    int best_u = -1;
+    uint64_t best_upc = 0, best_load = ~0ull;
+    for (int u = 0; u <= std::min(3, (int)req.n - 1); ++u) {
+        const uint64_t units = (uint64_t)req.batch << u;
+        const uint64_t upc = (units + std::min(units, sms) - 1) / std::min(units, sms);
+        const uint64_t load = upc << (req.n - u);  // leaves of the busiest CTA
+        if (upc > dev::kBfsMaxUnits || load > dev::kBfsMaxLeaves || units > 0xffffffffull) continue;
+        if (load < best_load) {
+            best_load = load;
+            best_u = u;
+            best_upc = upc;
+        }
+    }
+    if (best_u < 0) return PIR_ERR_UNSUPPORTED;
+    dev::BfsParams p{};
+    p.keys = req.dkeys;
+    p.key_bytes = (uint32_t)key_bytes(req.n);
+    p.n = req.n;
+    p.u = (uint32_t)best_u;
+    p.nunits = req.batch << best_u;
+    p.upc = (uint32_t)best_upc;
+    p.shares = shares;
+    p.ld = ld;
+    p.rows = req.row_hi;
+    p.vec2 = ((reinterpret_cast<uintptr_t>(shares) & 7u) == 0 && ld % 2 == 0) ? 1u : 0u;
+    p.status = req.dstatus;
+    const uint32_t ctas = (uint32_t)((p.nunits + best_upc - 1) / best_upc);
+    cudaError_t e = dev::smem_attribute_once(dev::expand_bfs_kernel, dev::kBfsSmemBytes);
+    for (int attempt = 0; e == cudaSuccess && attempt < 2; ++attempt) {
+        dev::expand_bfs_kernel<<<ctas, dev::kProducers, dev::kBfsSmemBytes, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaErrorInvalidValue || attempt > 0) break;
+        e = dev::smem_attribute_once(dev::expand_bfs_kernel, dev::kBfsSmemBytes, true);  // after a reset
+    }
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "expand_bfs launch");
+}
+
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream) {
     if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
+    {
+        const int rc = launch_expand_bfs(req, shares, ld, reinterpret_cast<cudaStream_t>(stream));
+        if (rc != PIR_ERR_UNSUPPORTED) return rc;
+    }
     dev::FusedParams p = make_params(req, plan);
     p.shares = shares;
     p.ld = ld;

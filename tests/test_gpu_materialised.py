@@ -42,6 +42,40 @@ def test_materialised_shares_match_oracle_full_eval(env, rows, batch, pad):
         assert (got[q, rows:] == M32).all()  # padding untouched
 
 
+@pytest.mark.parametrize("rows,batch,pad", [(1024, 1024, 0), (1000, 300, 1), (8192, 152, 0), (5, 7, 0), (2, 64, 3),
+                                            (3, 200, 0), (8191, 153, 2)])
+def test_many_small_trees_match_oracle_full_eval(env, rows, batch, pad):
+    """Batches of keys over small domains (partial batch retrieval's bins) run
+    breadth first, several keys per CTA, where a CTA's keys fit its level
+    buffers (8191 x 153 does not: two keys of 2^13 leaves per CTA, the item
+    kernel instead).  Every share vector equals the oracle's FullEval, with
+    AES-128 and ChaCha20 keys mixed in one batch, padded rows (odd ld) and one
+    bad key, whose vector is zero and which sets the status bit."""
+    torch, pir, orc = env
+    n = pir.pir_domain_bits(rows)
+    alphas = wl.alphas(rows + 3, rows, batch)
+    rnd = wl.key_randomness(rows + batch, n, batch)
+    keys = [orc.gen(n, int(a), 1 + q, r0, r1, c0, q % 2)[q % 3 == 1] for q, ((r0, r1, c0), a) in
+            enumerate(zip(rnd, alphas))]
+    bad_q = batch // 2
+    bad = bytearray(keys[bad_q])
+    bad[6] = 2  # party byte out of range
+    keys[bad_q] = bytes(bad)
+    ld = rows + pad
+    S = torch.full((batch, ld), -1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pir.pir_expand_materialise(rows, dev_keys(torch, keys), batch, S, status)
+    torch.cuda.synchronize()
+    got = S.cpu().numpy().view(np.uint32)
+    for q in range(batch):
+        if q == bad_q:
+            assert not got[q, :rows].any()
+        else:
+            assert np.array_equal(got[q, :rows], orc.full_eval(keys[q], rows)), q
+        assert (got[q, rows:] == M32).all()  # padding untouched
+    assert int(status.item()) & pir.PIR_STATUS_BAD_KEY
+
+
 def test_materialised_bad_key_gives_zero_vector_and_status(env):
     torch, pir, orc = env
     rows = 2000
