@@ -344,3 +344,44 @@ def test_host_entry_point_repeated_calls_and_streams(env):
         pir.pir_server_eval(dev_table(torch, T), b"".join(ks0), batch, out, stream=streams[i % 2])
         for q in range(batch):
             assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, q)
+
+
+def test_single_group_launches_overwrite_every_share(env):
+    """Launches whose batch is one query group (a lone query, or up to 8
+    queries) accumulate every CTA's sums into the output: outputs filled with
+    garbage first come back as the oracle's shares (the output is cleared in
+    stream order before the kernel adds into it), on repeated launches over
+    two streams, for an index-range shard too, and a bad key's share is zero."""
+    torch, pir, orc = env
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for rows, width, batch in [(1 << 16, 16, 1), (5000, 8, 2), (1 << 14, 64, 8), ((1 << 13) + 5, 4, 4)]:
+        n = pir.pir_domain_bits(rows)
+        T = wl.table_u32(rows + 2 * width, rows, width)
+        ks0, _ = make_keys(orc, n, wl.alphas(rows + 9, rows, batch), [1] * batch, rows + 11)
+        keys = list(ks0)
+        if batch > 1:
+            bad = bytearray(keys[-1])
+            bad[0] ^= 0xFF  # magic
+            keys[-1] = bytes(bad)
+        table = dev_table(torch, T)
+        dk = dev_keys(torch, keys)
+        want = [orc.answer(k, T) for k in keys[:batch - 1 if batch > 1 else 1]]
+        for rep in range(4):
+            st = streams[rep % 2]
+            out = torch.full((batch, width), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+            with torch.cuda.stream(st):
+                pir.pir_server_eval_device(table, dk, batch, out, stream=st)
+            st.synchronize()
+            got = out.cpu().numpy().view(np.uint32)
+            for q, w in enumerate(want):
+                assert np.array_equal(got[q], w), (rows, batch, rep, q)
+            if batch > 1:
+                assert not got[-1].any()
+    # an index-range shard with one query: rows [lo, hi) of a 5000-row domain
+    L, W, lo, hi = 5000, 16, 1024, 3000
+    T = wl.table_u32(77, L, W)
+    ks0, _ = make_keys(orc, pir.pir_domain_bits(L), [2500], [1], 78)
+    out = torch.full((1, W), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    pir.pir_server_eval_range(dev_table(torch, T[lo:hi]), lo, L, dev_keys(torch, ks0), 1, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32)[0], orc.answer(ks0[0], T, lo, hi))
