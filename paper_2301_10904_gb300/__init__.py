@@ -170,7 +170,11 @@ def _stream(stream):
 
 
 def table_of(t, rows: int | None = None) -> pir_table:
-    """pir_table describing a 2-D CUDA tensor of 32-bit words."""
+    """pir_table describing a 2-D CUDA tensor of 32-bit words; a pir_table is
+    returned as it is (a caller may build the descriptor once and pass it to
+    every call, as the C API's callers do)."""
+    if isinstance(t, pir_table):
+        return t
     assert t.dim() == 2 and t.element_size() == 4 and t.is_cuda and t.stride(1) == 1
     return pir_table(t.data_ptr(), t.shape[0] if rows is None else rows, t.shape[1], t.stride(0))
 
