@@ -472,10 +472,14 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  *    with accumulators in tensor memory): every u32 is split into four
  *    signed 8-bit limbs held exactly in fp16, the ten limb products of
  *    the low 32 bits accumulate exactly in fp32 for 256 values of k at a
- *    time and are then folded into u32 totals.  One CTA per SM (about
- *    200 KB of shared memory) holding its SM's tensor memory (512
- *    columns; 256 for 32-word tiles) while it runs, so a kernel that uses
- *    tensor memory on the same SM at the same time waits for it.  Its
+ *    time and are then folded into u32 totals.  With dshares and t->data
+ *    16-byte aligned and ld and t->stride multiples of 4 the raw tiles
+ *    arrive by tensor-map copies (PIR_TC_TENSOR_MAPS=0 in the environment
+ *    selects the kernel that loads them itself, as for other operands; the
+ *    result is the same).  One CTA per SM (up to 222 KB of shared memory)
+ *    holding its SM's tensor memory (512 columns; 256 for 32-word tiles)
+ *    while it runs, so a kernel that uses tensor memory on the same SM at
+ *    the same time waits for it.  Its
  *    waits are bounded like the scan's; one that gives up sets
  *    PIR_FAULT_WAIT_TIMEOUT, and then the whole launch's dout is invalid,
  *    not only that CTA's tile: the CTA frees its tensor memory after a

@@ -144,6 +144,18 @@ def test_materialised_pipeline_equals_fused_and_oracle(env):
     assert np.array_equal(rec.astype(np.uint32), T[alphas])
 
 
+# The tcgen05 engine has two kernels with one result: for 16-byte-aligned operands
+# the raw tiles arrive by tensor-map copies, otherwise (or with
+# PIR_TC_TENSOR_MAPS=0) the conversion warps load them.  The tests below run both.
+KERNELS = {"tensor_maps": "1", "loads": "0"}
+
+
+@pytest.fixture(params=sorted(KERNELS))
+def tc_kernel(request, monkeypatch):
+    monkeypatch.setenv("PIR_TC_TENSOR_MAPS", KERNELS[request.param])
+    return request.param
+
+
 def _tc_contract(torch, pir, S, T, pad=0):
     B, L = S.shape
     Sd = torch.zeros((B, L + pad), dtype=torch.int32)
@@ -158,12 +170,16 @@ def _tc_contract(torch, pir, S, T, pad=0):
 
 @pytest.mark.parametrize("B,L,W,pad", [
     (200, (1 << 16) + 77, 48, 0),   # 2 query tiles, several 256-k accumulator chunks per CTA, ragged k tail
+    (200, (1 << 16) + 77, 48, 3),   # the same with 16-byte-aligned share rows
     (129, 5000, 96, 0),             # one row in the second query tile; two word tiles, the second ragged
     (128, 20000, 32, 0),            # the 32-word tile shape
     (37, 3001, 33, 2),              # unaligned rows (ld % 4 != 0: scalar loads), ragged everywhere
     (300, 256, 64, 0),              # exactly one chunk per CTA
+    (5, 1000, 16, 0),               # batch and width below one tile: copies mostly past the edges
+    (1, 4, 4, 0),                   # k below one 32-value stage
+    (3, 70, 8, 2),                  # ragged k stage, aligned rows
 ])
-def test_tc_contract_matches_oracle(env, B, L, W, pad):
+def test_tc_contract_matches_oracle(env, tc_kernel, B, L, W, pad):
     torch, pir, orc = env
     rng = np.random.Generator(np.random.PCG64(B * 7 + L + W))
     S = rng.integers(0, 1 << 32, (B, L), dtype=np.uint64).astype(np.uint32)
@@ -171,7 +187,8 @@ def test_tc_contract_matches_oracle(env, B, L, W, pad):
     assert np.array_equal(_tc_contract(torch, pir, S, T, pad), orc.contract(S, T))
 
 
-def test_tc_contract_exact_at_the_accumulator_bound(env):
+@pytest.mark.parametrize("pad", [0, 3], ids=["ld_odd", "ld_aligned"])
+def test_tc_contract_exact_at_the_accumulator_bound(env, tc_kernel, pad):
     """0x7F7F7F80 splits into four signed limbs of -128, so every limb product
     is +2^14 and a class-3 accumulator reaches 4 * 2^14 * 256 = 2^24 just
     before it is drained: the largest value the exactness argument allows."""
@@ -181,12 +198,12 @@ def test_tc_contract_exact_at_the_accumulator_bound(env):
     T = np.full((L, W), 0x7F7F7F80, dtype=np.uint32)
     S[3, :] = 0x80808080  # limbs of mixed sign in one row
     T[:, 7] = 0xFFFFFFFF
-    assert np.array_equal(_tc_contract(torch, pir, S, T), orc.contract(S, T))
+    assert np.array_equal(_tc_contract(torch, pir, S, T, pad), orc.contract(S, T))
 
 
 @pytest.mark.parametrize("B,L,W,nrows,ncols", [(256, 1 << 20, 64, 6, 16), (1024, 1 << 24, 32, 4, 6)],
                          ids=["batched_2^20x64", "large_2^24x32"])
-def test_tc_contract_full_size_sampled_outputs(env, B, L, W, nrows, ncols):
+def test_tc_contract_full_size_sampled_outputs(env, tc_kernel, B, L, W, nrows, ncols):
     """The bench's full-size shapes, in the launch configuration the bench
     times: seeded random shares and table on the device, the tcgen05 product,
     and the oracle's product for a seeded sample of outputs (query rows x
