@@ -203,9 +203,16 @@ int pir_reconstruct(const uint32_t* s0, const uint32_t* s1, size_t w, uint32_t* 
  * keys: host, batch * pir_key_bytes(n) bytes back to back, every key with
  * n == pir_domain_bits(t->rows).  out: batch x width words, host or device
  * (detected).  With a host `out` the call returns after the result is
- * there.  Keys (and host-bound shares) are staged in stream-ordered device
- * memory from a pool the library creates per device, which keeps up to
- * 256 MiB of freed staging mapped between calls.  Errors: PIR_ERR_ARG,
+ * there.  A small call with a host `out` (keys and shares up to 32 KiB
+ * each) is staged in buffers of the calling thread (64 KiB of device and
+ * 96 KiB of pinned host memory per thread and device, kept until the thread
+ * exits) and runs as a CUDA graph built on the first call of its shape
+ * (table, batch, launch plan; up to 8 kept per thread): the keys and a
+ * zeroed share area reach the device in one copy, and the GPU runs that
+ * copy, the kernels and the copy back without waiting for the host between
+ * them.  Other calls stage keys (and host-bound shares) in stream-ordered
+ * device memory from a pool the library creates per device, which keeps up
+ * to 256 MiB of freed staging mapped between calls.  Errors: PIR_ERR_ARG,
  * PIR_ERR_KEY, PIR_ERR_DOMAIN, PIR_ERR_NOMEM, PIR_ERR_CUDA,
  * PIR_ERR_UNSUPPORTED, and, with a host `out`, PIR_ERR_TIMEOUT when a
  * bounded wait in this call's kernels gave up (the expand-and-scan and

@@ -250,42 +250,128 @@ static int eval_device(const pir_table* shard, uint64_t row_lo, uint32_t n, cons
     return run_plan(shard, row_lo, n, dkeys, batch, dout, dstatus, plan, stream);
 }
 
-// Device staging of the synchronous host-buffer path, per host thread and
-// device: keys and shares of a small call (a lone query, the latency-bound
-// case) without a stream-ordered allocation and free per call.  A call
-// returns only after its shares are back on the host, so the next call of
-// the same thread finds the buffer idle; the share area is cleared after the
-// copy back (stream-ordered, off the next call's critical path) and `cleared`
-// orders that clearing before the next call's kernel on whatever stream it
-// uses.  `zero_bytes`: how much of the share area, from its start, holds
-// zeros (a call writes only the first batch x width words).  Kept until the
-// thread exits.
+// Staging of the synchronous host-buffer path, per host thread and device,
+// for small calls (a lone query: the latency-bound case).  The keys and a
+// zeroed share area are laid out in mapped pinned host memory as they will
+// lie on the device and reach it in one copy; the call (that copy, the
+// kernels, the copy of the shares back to mapped pinned memory) runs as a
+// CUDA graph, built on the first call of its shape and kept, so that the GPU
+// runs the steps back to back instead of waiting for each host API call.
+// Both copies are small kernels reading and writing the host side directly,
+// not copy-engine transfers, whose start-up dominated at these sizes.  A
+// call returns only after its shares are on the host, so the buffers are
+// idle when the next call of the thread starts.  Kept until the thread exits.
 constexpr size_t kStageKeyBytes = 32u << 10, kStageShareBytes = 32u << 10;
-struct HostStage {
-    uint8_t* keys = nullptr;  // kStageKeyBytes, then kStageShareBytes of shares
-    cudaEvent_t copied = nullptr, cleared = nullptr;
-    size_t zero_bytes = 0;
-    ~HostStage() {
-        if (copied) cudaEventDestroy(copied);
-        if (cleared) cudaEventDestroy(cleared);
-        if (keys) cudaFree(keys);
+constexpr size_t kStageBytes = kStageKeyBytes + 256 + kStageShareBytes;
+constexpr size_t kStageGraphs = 8;  // graphs kept per thread and device (least recently used goes)
+
+struct StageShape {  // what a staged call's graph depends on
+    const uint32_t* table;
+    uint64_t rows, stride, batch;
+    uint32_t width, n;
+    pir_plan plan;
+    bool snap;
+    bool operator==(const StageShape& o) const {
+        return table == o.table && rows == o.rows && stride == o.stride && batch == o.batch && width == o.width &&
+               n == o.n && snap == o.snap && plan.group == o.plan.group && plan.range_log2 == o.plan.range_log2 &&
+               plan.vec == o.plan.vec && plan.ctas == o.plan.ctas && plan.strategy == o.plan.strategy &&
+               plan.tail_log2 == o.plan.tail_log2;
     }
+};
+
+struct HostStage {
+    uint8_t* dev = nullptr;   // device: keys, then the share area at a 256-byte boundary
+    uint8_t* hin = nullptr;   // mapped pinned host: the same layout, copied to `dev` in one piece
+    uint8_t* hout = nullptr;  // mapped pinned host: the shares copied back
+    uint32_t *hin_dev = nullptr, *hout_dev = nullptr;  // their device addresses
+    cudaStream_t capture = nullptr;
+    cudaEvent_t done = nullptr;
+    struct Graph {
+        StageShape shape;
+        cudaGraphExec_t exec;  // nullptr: this shape could not be captured (the pool path runs it)
+        uint64_t used;
+    };
+    std::vector<Graph> graphs;
+    uint64_t tick = 0;
+    ~HostStage() {
+        for (Graph& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (done) cudaEventDestroy(done);
+        if (capture) cudaStreamDestroy(capture);
+        if (hout) cudaFreeHost(hout);
+        if (hin) cudaFreeHost(hin);
+        if (dev) cudaFree(dev);
+    }
+    static size_t share_offset(size_t key_bytes) { return (key_bytes + 255) & ~size_t(255); }
 };
 static HostStage* host_stage() {
     thread_local HostStage stages[kMaxDevices];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     HostStage& st = stages[dev];
-    if (!st.keys) {
-        if (cudaMalloc((void**)&st.keys, kStageKeyBytes + kStageShareBytes) != cudaSuccess ||
-            cudaEventCreateWithFlags(&st.copied, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&st.cleared, cudaEventDisableTiming) != cudaSuccess) {
+    if (!st.dev) {
+        if (cudaMalloc((void**)&st.dev, kStageBytes) != cudaSuccess ||
+            cudaHostAlloc((void**)&st.hin, kStageBytes, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void**)&st.hout, kStageShareBytes, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&st.hin_dev, st.hin, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&st.hout_dev, st.hout, 0) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&st.capture, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
-            return nullptr;  // the caller falls back to the pool
+            if (st.done) cudaEventDestroy(st.done);
+            if (st.capture) cudaStreamDestroy(st.capture);
+            if (st.hin) cudaFreeHost(st.hin);
+            if (st.hout) cudaFreeHost(st.hout);
+            if (st.dev) cudaFree(st.dev);
+            st.done = nullptr;
+            st.capture = nullptr;
+            st.hin = st.hout = nullptr;
+            st.hin_dev = st.hout_dev = nullptr;
+            st.dev = nullptr;
+            return nullptr;  // the caller takes the pool path
         }
-        st.zero_bytes = 0;
     }
     return &st;
+}
+
+// The graph of a staged call of shape `sh` (keys of `kb` bytes each, shares of
+// `out_bytes`), built on first use: the one copy of keys and zeroed shares to
+// the device, the fault-word snapshots around the kernels when `snap` is
+// given, the kernels, the shares' copy back.  nullptr when the shape could
+// not be captured (the caller then takes the pool path; the answer is kept).
+static cudaGraphExec_t stage_graph(HostStage& st, const StageShape& sh, const pir_table* t, size_t kb,
+                                   size_t out_bytes, uint32_t* snap, uint32_t* fault_word) {
+    for (HostStage::Graph& g : st.graphs)
+        if (g.shape == sh) {
+            g.used = ++st.tick;
+            return g.exec;
+        }
+    const size_t ks = HostStage::share_offset(sh.batch * kb);
+    uint32_t* dout = reinterpret_cast<uint32_t*>(st.dev + ks);
+    cudaStream_t c = st.capture;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(c, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        bool ok = launch_words_copy(st.hin_dev, reinterpret_cast<uint32_t*>(st.dev), (ks + out_bytes) / 4, c) == PIR_OK;
+        if (ok && snap)
+            ok = cudaMemcpyAsync(&snap[0], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, c) == cudaSuccess;
+        if (ok) ok = run_plan(t, 0, sh.n, st.dev, sh.batch, dout, nullptr, sh.plan, c, /*zeroed=*/true) == PIR_OK;
+        if (ok && snap)
+            ok = cudaMemcpyAsync(&snap[1], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, c) == cudaSuccess;
+        if (ok) ok = launch_words_copy(dout, st.hout_dev, out_bytes / 4, c) == PIR_OK;
+        const bool ended = cudaStreamEndCapture(c, &graph) == cudaSuccess;
+        if (ok && ended && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();  // a capture that failed leaves its error here, not for the caller's next call
+    if (st.graphs.size() >= kStageGraphs) {
+        auto lru = std::min_element(st.graphs.begin(), st.graphs.end(),
+                                    [](const HostStage::Graph& a, const HostStage::Graph& b) { return a.used < b.used; });
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        st.graphs.erase(lru);
+    }
+    st.graphs.push_back({sh, exec, ++st.tick});
+    return exec;
 }
 
 // Two words of pinned host memory per host thread, for stream-ordered
@@ -601,31 +687,48 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
     // during this call turns into PIR_ERR_TIMEOUT once the call synchronizes
     uint32_t* snap = !out_on_device && strategy_waits(plan.strategy) ? fault_snapshots() : nullptr;
     uint32_t* fault_word = snap ? device_fault_word() : nullptr;
+    if (!fault_word) snap = nullptr;
+    cudaError_t e = cudaSuccess;
     HostStage* st = !out_on_device && batch * kb <= kStageKeyBytes && out_bytes <= kStageShareBytes &&
                             plan.strategy != PIR_STRATEGY_EXPAND_SCAN
                         ? host_stage()
                         : nullptr;
+    if (st) {
+        // the staged graph: keys and zeroed shares in pinned memory, one launch, shares back
+        const size_t key_total = batch * kb, ks = HostStage::share_offset(key_total);
+        std::memcpy(st->hin, keys, key_total);
+        std::memset(st->hin + key_total, 0, ks - key_total + out_bytes);
+        StageShape sh{t->data, t->rows, t->stride, batch, t->width, n, plan, snap != nullptr};
+        cudaGraphExec_t exec = stage_graph(*st, sh, t, kb, out_bytes, snap, fault_word);
+        if (exec) {
+            e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(st->done, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(st->done);
+            if (e != cudaSuccess) {
+                rc = cuda_fail((int)e, "staged call");
+                cudaStreamSynchronize(s);
+                return rc;
+            }
+            std::memcpy(out, st->hout, out_bytes);
+            if (snap && (snap[1] & ~snap[0] & PIR_FAULT_WAIT_TIMEOUT)) return PIR_ERR_TIMEOUT;
+            return PIR_OK;
+        }
+    }
+    // stream-ordered staging from the pool
     uint8_t* dkeys = nullptr;
     uint32_t* dout = nullptr;
     cudaMemPool_t pool = nullptr;
-    cudaError_t e = cudaSuccess;
-    if (st) {
-        dkeys = st->keys;
-        dout = reinterpret_cast<uint32_t*>(st->keys + kStageKeyBytes);
-        if (st->zero_bytes) CUDA_TRY(cudaStreamWaitEvent(s, st->cleared, 0), "wait staging cleared");
-    } else {
-        rc = staging_pool(&pool);
-        if (rc != PIR_OK) return rc;
-        CUDA_TRY(cudaMallocFromPoolAsync((void**)&dkeys, batch * kb, pool, s), "alloc keys");
-        if (!out_on_device) {
-            e = cudaMallocFromPoolAsync((void**)&dout, out_bytes, pool, s);
-            if (e != cudaSuccess) {
-                cudaFreeAsync(dkeys, s);
-                return cuda_fail((int)e, "alloc shares");
-            }
-        } else {
-            dout = out;
+    rc = staging_pool(&pool);
+    if (rc != PIR_OK) return rc;
+    CUDA_TRY(cudaMallocFromPoolAsync((void**)&dkeys, batch * kb, pool, s), "alloc keys");
+    if (!out_on_device) {
+        e = cudaMallocFromPoolAsync((void**)&dout, out_bytes, pool, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dkeys, s);
+            return cuda_fail((int)e, "alloc shares");
         }
+    } else {
+        dout = out;
     }
     e = cudaMemcpyAsync(dkeys, keys, batch * kb, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) rc = cuda_fail((int)e, "copy keys");
@@ -633,9 +736,7 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
         e = cudaMemcpyAsync(&snap[0], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
     }
-    const size_t zero_before = st ? st->zero_bytes : 0;
-    if (rc == PIR_OK) rc = run_plan(t, 0, n, dkeys, batch, dout, nullptr, plan, stream, st && out_bytes <= zero_before);
-    if (st) st->zero_bytes = 0;
+    if (rc == PIR_OK) rc = run_plan(t, 0, n, dkeys, batch, dout, nullptr, plan, stream);
     if (rc == PIR_OK && fault_word) {
         e = cudaMemcpyAsync(&snap[1], fault_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "fault word snapshot");
@@ -644,23 +745,11 @@ int pir_server_eval(const pir_table* t, const uint8_t* keys, size_t batch, uint3
         e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail((int)e, "copy shares");
     }
-    if (st) {
-        // the shares are on their way back: clear the share area for the next
-        // call behind them, and wait for the copy alone
-        if (rc == PIR_OK) e = cudaEventRecord(st->copied, s);
-        if (rc == PIR_OK && e == cudaSuccess) e = cudaMemsetAsync(dout, 0, out_bytes, s);
-        if (rc == PIR_OK && e == cudaSuccess) e = cudaEventRecord(st->cleared, s);
-        if (rc == PIR_OK && e == cudaSuccess) st->zero_bytes = std::max(out_bytes, zero_before);
-        if (rc == PIR_OK && e != cudaSuccess) rc = cuda_fail((int)e, "staging clear");
-        e = rc == PIR_OK ? cudaEventSynchronize(st->copied) : cudaStreamSynchronize(s);
+    if (!out_on_device) cudaFreeAsync(dout, s);
+    cudaFreeAsync(dkeys, s);
+    if (!out_on_device) {
+        e = cudaStreamSynchronize(s);
         if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
-    } else {
-        if (!out_on_device) cudaFreeAsync(dout, s);
-        cudaFreeAsync(dkeys, s);
-        if (!out_on_device) {
-            e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess && rc == PIR_OK) rc = cuda_fail((int)e, "synchronize");
-        }
     }
     if (rc == PIR_OK && fault_word && (snap[1] & ~snap[0] & PIR_FAULT_WAIT_TIMEOUT)) rc = PIR_ERR_TIMEOUT;
     return rc;

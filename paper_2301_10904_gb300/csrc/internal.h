@@ -133,6 +133,9 @@ int launch_scan(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint3
 bool scan_bins_supported(const uint32_t* table, uint64_t stride, uint32_t width, uint64_t bin_rows);
 int launch_scan_bins(const uint32_t* shares, const uint32_t* table, uint64_t stride, uint32_t width, uint64_t rows,
                      uint64_t bin_rows, uint32_t* out, void* stream);
+// dst[i] = src[i] for i < words by a kernel (scan.cu): either side may be
+// pinned host memory mapped into the device's address space
+int launch_words_copy(const uint32_t* src, uint32_t* dst, uint64_t words, void* stream);
 // diagnostic: a bounded wait that must run out (scan.cu)
 int selftest_bounded_wait(uint32_t polls, void* stream);
 // library-wide device fault bits (PIR_FAULT_*), read on the current device

@@ -240,7 +240,25 @@ __global__ void wait_selftest_kernel(uint32_t polls, uint32_t* gave_up) {
     *gave_up = done ? 0u : 1u;
 }
 
+// dst[i] = src[i] for i < words, either side in device memory or in pinned
+// host memory mapped into the device's address space (the staged host call's
+// keys in and shares out).  Reads bypass the caches (the host rewrites its
+// side between launches).
+__global__ void __launch_bounds__(256) words_copy_kernel(const uint32_t* __restrict__ src,
+                                                         uint32_t* __restrict__ dst, uint64_t words) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = __ldcv(src + i);
+}
+
 }  // namespace dev
+
+int launch_words_copy(const uint32_t* src, uint32_t* dst, uint64_t words, void* stream) {
+    if (words == 0) return PIR_OK;
+    const uint64_t blocks = std::min<uint64_t>((words + 255) / 256, 64);
+    dev::words_copy_kernel<<<(uint32_t)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, dst, words);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "words copy launch");
+}
 
 int selftest_bounded_wait(uint32_t polls, void* stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

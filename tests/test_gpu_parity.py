@@ -328,11 +328,14 @@ def test_library_keys_on_gpu_reconstruct(env):
 
 
 def test_host_entry_point_repeated_calls_and_streams(env):
-    """Small synchronous calls reuse one staging buffer per host thread and
-    device, whose share area is cleared after each call's copy back: calls of
-    growing and shrinking widths and batches, on two streams in turn, each
-    match the oracle word for word (stale or partly cleared staging would
-    show up here)."""
+    """Small synchronous calls run through one staging area per host thread
+    and device, as a graph kept per call shape (table, batch, plan), whose
+    one copy in brings the keys and a zeroed share area: calls of growing and
+    shrinking widths and batches on new tables (more shapes than the graphs
+    kept, so some are dropped and rebuilt), on two streams in turn, then one
+    shape again and again with new keys and the table's contents replaced in
+    place; each share matches the oracle word for word (stale keys, a share
+    area not cleared, or a graph holding old contents would show up here)."""
     torch, pir, orc = env
     streams = [torch.cuda.Stream(), torch.cuda.current_stream()]
     cases = [(3000, 8, 1), (3000, 64, 3), (5000, 16, 7), (3000, 8, 2), (1 << 12, 128, 4), (5000, 16, 1)]
@@ -342,6 +345,20 @@ def test_host_entry_point_repeated_calls_and_streams(env):
         ks0, _ = make_keys(orc, n, wl.alphas(i, rows, batch), [1] * batch, 90 + i)
         out = np.full((batch, width), 0x5A5A5A5A, np.uint32)
         pir.pir_server_eval(dev_table(torch, T), b"".join(ks0), batch, out, stream=streams[i % 2])
+        for q in range(batch):
+            assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, q)
+    rows, width = 5000, 16
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(77, rows, width)
+    table = dev_table(torch, T)
+    for i in range(8):
+        if i == 4:
+            T = wl.table_u32(78, rows, width)
+            table.copy_(dev_table(torch, T))
+        batch = 1 + (i % 2)
+        ks0, _ = make_keys(orc, n, wl.alphas(200 + i, rows, batch), [1] * batch, 300 + i)
+        out = np.full((batch, width), 0x5A5A5A5A, np.uint32)
+        pir.pir_server_eval(table, b"".join(ks0), batch, out, stream=streams[i % 2])
         for q in range(batch):
             assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, q)
 
