@@ -446,7 +446,10 @@ class SingleTableWorkload:
                            "peak_basis": tbasis + " (bf16 burst; fp16 dense is the same nominal rate)"},
                 "hbm": {"achieved": round(gbs, 1), "peak": hpeak, "unit": "GB/s", "frac": round(gbs / hpeak, 4),
                         "peak_basis": hbasis},
-                "kernel": "contract_tc_kernel", "ms": round(ms, 4)}
+                # the share matrix here is a fresh aligned tensor (ld = rows), so the
+                # tensor-map kernel runs unless the environment selects the other one
+                "kernel": ("contract_tc_kernel" if os.environ.get("PIR_TC_TENSOR_MAPS", "1").startswith("0")
+                           or self.rows % 4 or self.width % 4 else "contract_tc2_kernel"), "ms": round(ms, 4)}
 
     def extras(self):
         torch, pir, stream = self.torch, self.pir, self.stream
