@@ -501,9 +501,10 @@ int pir_expand_materialise(uint64_t rows, const uint8_t* dkeys, size_t batch, ui
  *    gives up leaves dout incomplete and sets PIR_FAULT_WAIT_TIMEOUT (see
  *    pir_device_status);
  *  - PIR_CONTRACT_AUTO: the fastest of these as measured on GB300 for the
- *    shape: the streaming scan for at most 24 queries where its layout
- *    conditions hold, the tcgen05 engine otherwise (IMAD and the u8-limb
- *    MMAs are slower than one of the two at every batch).
+ *    shape: the streaming scan for at most 16 queries (32 when t->width <=
+ *    32) where its layout conditions hold, the tcgen05 engine otherwise
+ *    (IMAD and the u8-limb MMAs are slower than one of the two at every
+ *    batch).
  * dout (device, batch x width) is overwritten.  Asynchronous. */
 int pir_contract_u32(const uint32_t* dshares, uint64_t ld, size_t batch, const pir_table* t, uint32_t* dout,
                      int engine, void* stream);

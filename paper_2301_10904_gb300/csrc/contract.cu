@@ -237,16 +237,21 @@ __global__ void __launch_bounds__(256) contract_mma_u8_kernel(const uint32_t* __
 
 // Largest batch for which PIR_CONTRACT_AUTO picks the streaming scan.  The
 // scan reads the table once per 8 queries; the tcgen05 engine converts a
-// whole 128-query tile whatever the batch.  On GB300, 2^20 x 64 words: scan
-// 0.046 / 0.059 / 0.115 / 0.229 ms at 1 / 8 / 16 / 32 queries, tcgen05
-// 0.22 ms for any batch up to 128 (IMAD 0.32-0.68 ms, never the fastest).
-constexpr uint32_t kAutoScanMaxBatch = 24;
+// whole 128-query tile whatever the batch, and with rows of 32 words or fewer
+// each share word feeds half as many products.  On GB300 (ms, scan / tcgen05):
+// 2^20 x 64 words 0.116 / 0.167 at 16 queries, 0.170 / 0.168 at 24;
+// 2^18 x 128 words 0.066 / 0.095 at 16, 0.098 / 0.093 at 24; 2^22 x 32 words
+// 0.453 / 0.572 at 32, 0.568 / 0.573 at 40.  IMAD is never the fastest.
+constexpr uint32_t kAutoScanMaxBatchWide = 16;    // rows wider than 32 words
+constexpr uint32_t kAutoScanMaxBatchNarrow = 32;  // rows of at most 32 words
 
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
                     uint32_t width, uint64_t rows, uint32_t* out, int engine, void* stream) {
     if (engine == PIR_CONTRACT_AUTO)  // the engine measured fastest for the shape on GB300
-        engine = batch <= kAutoScanMaxBatch && scan_supported(shares, ld, table, stride, width) ? PIR_CONTRACT_SCAN
-                                                                                                 : PIR_CONTRACT_TC_F16;
+        engine = batch <= (width <= 32 ? kAutoScanMaxBatchNarrow : kAutoScanMaxBatchWide) &&
+                         scan_supported(shares, ld, table, stride, width)
+                     ? PIR_CONTRACT_SCAN
+                     : PIR_CONTRACT_TC_F16;
     if (engine == PIR_CONTRACT_SCAN) return launch_scan(shares, ld, batch, table, stride, width, rows, out, stream);
     if (engine == PIR_CONTRACT_TC_F16)
         return launch_contract_tc(shares, ld, batch, table, stride, width, rows, out, stream);

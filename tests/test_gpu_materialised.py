@@ -95,7 +95,8 @@ def test_materialised_bad_key_gives_zero_vector_and_status(env):
 @pytest.mark.parametrize("engine", [0, 1, 3, 4], ids=["imad", "mma_u8", "tc_f16", "auto"])
 @pytest.mark.parametrize("B,L,W", [(1, 1, 1), (3, 100, 5), (64, 4096, 64), (70, 3000, 65), (256, 1 << 14, 16),
                                    (5, 777, 128), (9, 20000, 32), (6, 4096, 32), (20, 4096, 64),
-                                   (24, 2048, 16), (25, 2048, 16)])  # both sides of the AUTO switch
+                                   (32, 2048, 16), (33, 2048, 16),  # both sides of the AUTO switch, narrow rows
+                                   (16, 2048, 64), (17, 2048, 64)])  # and wide rows
 def test_contract_matches_oracle(env, B, L, W, engine):
     torch, pir, orc = env
     rng = np.random.Generator(np.random.PCG64(B * L + W))
