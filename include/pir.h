@@ -519,6 +519,16 @@ int pir_plan_for(uint64_t rows, uint32_t width, size_t batch, pir_plan* plan);
  * Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN, PIR_ERR_UNSUPPORTED (width). */
 int pir_plan_inspect(uint64_t rows, uint32_t width, size_t batch, uint32_t sms, pir_plan* plan);
 
+/* Pins `plan` for evaluations of this table shape and batch: stores it where
+ * pir_autotune stores its winner, for (current device, t->rows, t->width,
+ * batch rounded up to a power of two, whether 128-bit loads apply), after
+ * the checks of an explicit plan (pir_server_eval_device_plan).  Restores a
+ * plan measured in an earlier process, or fixes one for a deployment.  A NULL
+ * `plan` removes the entry, so that the heuristic answers again.  Host only
+ * (no launch).  Errors: PIR_ERR_ARG, PIR_ERR_DOMAIN, PIR_ERR_UNSUPPORTED
+ * (a plan outside the kernels' limits for this table). */
+int pir_plan_pin(const pir_table* t, size_t batch, const pir_plan* plan);
+
 /* Autotuner of the single-table strategy and launch shape (the paper tunes
  * batch and strategy per table size, Sec. 3.2.1 and 3.2.5): times, on this
  * table and batch (device keys dkeys, device shares dout; synchronizes

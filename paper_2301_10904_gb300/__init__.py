@@ -134,6 +134,7 @@ def _load():
         "pir_autotune": (ctypes.c_int, [ctypes.POINTER(pir_table), u8p, ctypes.c_size_t, u32p, vp,
                                         ctypes.POINTER(pir_plan), ctypes.POINTER(ctypes.c_float)]),
         "pir_plan_for": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
+        "pir_plan_pin": (ctypes.c_int, [ctypes.POINTER(pir_table), ctypes.c_size_t, ctypes.POINTER(pir_plan)]),
         "pir_plan_inspect": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_uint32,
                                             ctypes.POINTER(pir_plan)]),
         "pir_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
@@ -599,6 +600,13 @@ class Server:
 
 def pir_server_create(**cfg) -> Server:
     return Server(**cfg)
+
+
+def pir_plan_pin(table, batch: int, plan=None):
+    """Pins `plan` (a pir_plan) for this table shape and batch size, as if the
+    autotuner had chosen it; None removes the entry (the heuristic answers)."""
+    _check(_lib.pir_plan_pin(ctypes.byref(table_of(table)), batch, ctypes.byref(plan) if plan is not None else None),
+           "pir_plan_pin")
 
 
 def pir_autotune(table, dkeys, batch: int, dout, stream=None):

@@ -430,6 +430,27 @@ int pir_plan_inspect(uint64_t rows, uint32_t width, size_t batch, uint32_t sms, 
     return heuristic_plan(rows, width, batch, (int)sms, plan);
 }
 
+int pir_plan_pin(const pir_table* t, size_t batch, const pir_plan* plan) {
+    using namespace pir;
+    if (!table_ok(t) || batch == 0 || batch > 0xffffffffu) return PIR_ERR_ARG;
+    const uint32_t n = pir_domain_bits(t->rows);
+    if (n == 0) return PIR_ERR_DOMAIN;
+    const bool v = vec_ok(t);
+    const ShapeKey key = shape_key(t->rows, t->width, batch, v);
+    if (!plan) {
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        g_tuned.erase(key);
+        return PIR_OK;
+    }
+    // the checks of an explicit plan (pir_server_eval_device_plan)
+    pir_plan checked{};
+    const int rc = resolve_plan(t, 0, n, batch, plan, &checked);
+    if (rc != PIR_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_tuned[key] = checked;
+    return PIR_OK;
+}
+
 int pir_autotune(const pir_table* t, const uint8_t* dkeys, size_t batch, uint32_t* dout, void* stream,
                  pir_plan* best_plan, float* best_ms) {
     using namespace pir;

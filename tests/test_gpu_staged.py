@@ -207,3 +207,34 @@ def test_staged_full_size_2p24x32_one_query(env):
     assert np.array_equal(g0, w0) and np.array_equal(g1, w1)
     assert np.array_equal(pir.pir_reconstruct(g0, g1), T[alpha])
     assert pir.pir_device_status(clear=True) == 0
+
+
+def test_staged_strategy_through_the_host_entry_point(env):
+    """A staged plan pinned for the shape runs through pir_server_eval's
+    graph (keys in, the staged kernel between two snapshots of the device
+    fault word, shares out): calls with new keys on the same graph give the
+    oracle's shares, and a fault bit left set before the calls (by the
+    bounded-wait diagnostic) is not reported as theirs."""
+    torch, pir, orc = env
+    rows, W, batch = (1 << 15) + 1000, 32, 2
+    n = pir.pir_domain_bits(rows)
+    T = wl.table_u32(91, rows, W)
+    table = dev_table(torch, T)
+    plan = staged_plan(pir, rows, W, batch)
+    pir.pir_plan_pin(table, batch, plan)
+    try:
+        assert pir.pir_plan_for(rows, W, batch).strategy == STAGED
+        pir.pir_device_status(clear=True)
+        assert pir.pir_selftest_bounded_wait(4096) == -6  # leaves PIR_FAULT_WAIT_TIMEOUT set
+        for i in range(3):
+            ks0, ks1 = make_keys(orc, n, wl.alphas(500 + i, rows, batch), [1] * batch, 600 + i)
+            out0 = np.full((batch, W), 0x5A5A5A5A, np.uint32)
+            out1 = np.full((batch, W), 0x5A5A5A5A, np.uint32)
+            pir.pir_server_eval(table, b"".join(ks0), batch, out0)  # raises on PIR_ERR_TIMEOUT
+            pir.pir_server_eval(table, b"".join(ks1), batch, out1)
+            for q in range(batch):
+                assert np.array_equal(out0[q], orc.answer(ks0[q], T)), (i, q)
+                assert np.array_equal(out1[q], orc.answer(ks1[q], T)), (i, q)
+        assert pir.pir_device_status(clear=True) == pir.PIR_FAULT_WAIT_TIMEOUT  # the diagnostic's bit only
+    finally:
+        pir.pir_plan_pin(table, batch, None)

@@ -93,3 +93,31 @@ def test_inspect_rejects_bad_arguments(pir):
         with pytest.raises(pir.PirError) as e:
             pir.pir_plan_inspect(*args)
         assert e.value.code == -1, args
+
+
+def test_pinned_plan_is_answered_per_batch_bucket_and_removed(pir):
+    """pir_plan_pin stores a checked plan where the autotuner stores its winner
+    (batch rounded up to a power of two): pir_plan_for answers it for every
+    batch of that bucket, not for the next bucket, and the heuristic's answer
+    returns once the entry is removed.  A plan outside the kernels' limits is
+    refused.  Host only: the table descriptor is never dereferenced."""
+    rows, width = 1 << 16, 64
+    t = pir.pir_table(0x100000, rows, width, width)  # a 16-byte-aligned descriptor, no memory behind it
+    before = {b: pir.pir_plan_for(rows, width, b).as_dict() for b in (3, 4, 5)}
+    pin = pir.pir_plan(2, 10, 4, 0, pir.PIR_STRATEGY_FUSED, 0)
+    pir.pir_plan_pin(t, 3, pin)
+    try:
+        for b in (3, 4):
+            got = pir.pir_plan_for(rows, width, b)
+            assert (got.group, got.range_log2, got.vec, got.strategy) == (2, 10, 4, pir.PIR_STRATEGY_FUSED)
+        assert pir.pir_plan_for(rows, width, 5).as_dict() == before[5]
+        staged = pir.pir_plan(2, 9, 4, 0, pir.PIR_STRATEGY_FUSED_STAGED, 0)
+        pir.pir_plan_pin(t, 4, staged)  # same bucket: replaces the entry
+        assert pir.pir_plan_for(rows, width, 3).strategy == pir.PIR_STRATEGY_FUSED_STAGED
+        with pytest.raises(pir.PirError) as e:
+            pir.pir_plan_pin(t, 3, pir.pir_plan(2, 17, 4, 0, pir.PIR_STRATEGY_FUSED, 0))  # 2^17 rows per item > 2^16
+        assert e.value.code in (-1, -8)
+        assert pir.pir_plan_for(rows, width, 3).strategy == pir.PIR_STRATEGY_FUSED_STAGED  # left as it was
+    finally:
+        pir.pir_plan_pin(t, 3, None)
+    assert {b: pir.pir_plan_for(rows, width, b).as_dict() for b in (3, 4, 5)} == before
