@@ -363,6 +363,28 @@ def test_host_entry_point_repeated_calls_and_streams(env):
             assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, q)
 
 
+def test_host_entry_point_at_the_staging_limits(env):
+    """The host call stages keys and shares of up to 32 KiB each in the calling
+    thread's buffers (one graph per shape) and takes the stream-ordered pool
+    beyond that: calls just inside both limits and just past each of them
+    give the oracle's shares word for word, on both sides twice."""
+    torch, pir, orc = env
+    rows = 1 << 16
+    n = pir.pir_domain_bits(rows)
+    kb = pir.pir_key_bytes(n)
+    inside = (32 << 10) // kb  # keys just inside 32 KiB
+    cases = [(inside, 8), (inside + 1, 8),  # key bytes: staged, then pooled
+             (8, 1024), (9, 1024)]  # share bytes: 32 KiB, then past it (1024 words: the widest fused rows)
+    for i, (batch, width) in enumerate(cases * 2):
+        T = wl.table_u32(700 + width, rows, width)
+        table = dev_table(torch, T)
+        ks0, _ = make_keys(orc, n, wl.alphas(710 + i, rows, batch), [1] * batch, 720 + i)
+        out = np.full((batch, width), 0x5A5A5A5A, np.uint32)
+        pir.pir_server_eval(table, b"".join(ks0), batch, out)
+        for q in sorted({0, batch // 2, batch - 1}):
+            assert np.array_equal(out[q], orc.answer(ks0[q], T)), (i, batch, width, q)
+
+
 def test_single_group_launches_overwrite_every_share(env):
     """Launches whose batch is one query group (a lone query, or up to 8
     queries) accumulate every CTA's sums into the output: outputs filled with
