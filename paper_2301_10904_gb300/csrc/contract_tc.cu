@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -597,60 +598,87 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const uint32_t n4 = (cw % kN8) * 8u + (lane & 7u), qt = (cw / kN8) * 4u + (lane >> 3);
         const bool has_t = qt < kT2StageK / 4u;
         const uint32_t rot = (n4 >> 1) & 3u;
-        for (uint32_t g = 0; g < nst; ++g) {
-            const uint32_t r = g % S2::kRawStages, pq = g % S2::kPlaneStages;
-            // warp-uniform waits: the lanes meet in __syncwarp below
-            if (!__all_sync(0xffffffffu, wait_bounded(base + S2::kRawFull + 8u * r, (g / S2::kRawStages) & 1u,
-                                                      abort_flag, p.faults)))
-                break;
-            const char* rawp = gbase + (raw_stage(r) - base);
-            uint4 a[4], u[4];
+        // Query rows past the batch are zeros in every stage: their plane rows are
+        // cleared once here (ordered before the tensor core's first read by the first
+        // stage's proxy fence) and never converted.
+        const uint32_t rows_valid = p.B - m0 < kTcM ? p.B - m0 : kTcM;
+        if (rows_valid < kTcM) {
+            for (uint32_t pq = 0; pq < S2::kPlaneStages; ++pq)
 #pragma unroll
-            for (int it = 0; it < 4; ++it)
-                a[it] = *reinterpret_cast<const uint4*>(rawp + ((uint32_t)it * 32u + rs) * (kT2StageK * 4u) + q * 16u);
-            if (has_t) {
+                for (int it = 0; it < 4; ++it) {
+                    const uint32_t row = (uint32_t)it * 32u + rs;
+                    if (row >= rows_valid)
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    u[e] = *reinterpret_cast<const uint4*>(rawp + kT2RawA + (4u * qt + e) * ((uint32_t)TN * 4u) +
-                                                           n4 * 16u);
-            }
-            if (!__all_sync(0xffffffffu, wait_bounded(base + S2::kPlEmpty + 8u * pq,
-                                                      ((g / S2::kPlaneStages) & 1u) ^ 1u, abort_flag, p.faults)))
-                break;
-            const uint32_t plane = plane_stage(pq);
-#pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                uint2 pl[4];
-                limbs4(a[it].x, a[it].y, a[it].z, a[it].w, pl);
-                const uint32_t off = sw64_off((uint32_t)it * 32u + rs, q);
-#pragma unroll
-                for (int pp = 0; pp < 4; ++pp) sts64(plane + pp * kT2PlaneA + off, pl[pp]);
-            }
-            if (has_t) {
-                // u[e] = words 4 n4 .. of k row 4 qt + e, rotated: word j = word (j + rot) % 4
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (rot & 1u) u[e] = make_uint4(u[e].y, u[e].z, u[e].w, u[e].x);
-                    if (rot & 2u) u[e] = make_uint4(u[e].z, u[e].w, u[e].x, u[e].y);
+                        for (int pp = 0; pp < 4; ++pp)
+                            sts64(plane_stage(pq) + pp * kT2PlaneA + sw64_off(row, q), make_uint2(0u, 0u));
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    uint2 pl[4];
-                    limbs4(word_of(u[0], j), word_of(u[1], j), word_of(u[2], j), word_of(u[3], j), pl);
-                    const uint32_t off = sw64_off(4u * n4 + ((j + rot) & 3u), qt);
-#pragma unroll
-                    for (int pp = 0; pp < 4; ++pp) sts64(plane + 4u * kT2PlaneA + pp * S2::kPlaneB + off, pl[pp]);
-                }
-            }
-            // The tensor core reads the planes, and the next copy into the raw stage writes,
-            // through the async proxy: one fence orders this thread's plane stores and raw
-            // reads before both.  (Releasing the raw stage before the conversion, with its own
-            // fence, measured slower; without that fence the copy overwrote words not yet read.)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(base + S2::kPlFull + 8u * pq);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(base + S2::kRawEmpty + 8u * r);  // one arrival per warp
         }
+        // The loop, compiled once for a full tile (no row checks: they cost a full
+        // tile 8 % when present) and once for a tile with rows past the batch.
+        auto convert_all = [&](auto full) {
+            constexpr bool kFull = decltype(full)::value;
+            for (uint32_t g = 0; g < nst; ++g) {
+                const uint32_t r = g % S2::kRawStages, pq = g % S2::kPlaneStages;
+                // warp-uniform waits: the lanes meet in __syncwarp below
+                if (!__all_sync(0xffffffffu, wait_bounded(base + S2::kRawFull + 8u * r, (g / S2::kRawStages) & 1u,
+                                                          abort_flag, p.faults)))
+                    break;
+                const char* rawp = gbase + (raw_stage(r) - base);
+                uint4 a[4], u[4];
+#pragma unroll
+                for (int it = 0; it < 4; ++it)
+                    if (kFull || (uint32_t)it * 32u + rs < rows_valid)
+                        a[it] = *reinterpret_cast<const uint4*>(rawp + ((uint32_t)it * 32u + rs) * (kT2StageK * 4u) +
+                                                                q * 16u);
+                if (has_t) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        u[e] = *reinterpret_cast<const uint4*>(rawp + kT2RawA + (4u * qt + e) * ((uint32_t)TN * 4u) +
+                                                               n4 * 16u);
+                }
+                if (!__all_sync(0xffffffffu, wait_bounded(base + S2::kPlEmpty + 8u * pq,
+                                                          ((g / S2::kPlaneStages) & 1u) ^ 1u, abort_flag, p.faults)))
+                    break;
+                const uint32_t plane = plane_stage(pq);
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    if (!kFull && (uint32_t)it * 32u + rs >= rows_valid) continue;
+                    uint2 pl[4];
+                    limbs4(a[it].x, a[it].y, a[it].z, a[it].w, pl);
+                    const uint32_t off = sw64_off((uint32_t)it * 32u + rs, q);
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) sts64(plane + pp * kT2PlaneA + off, pl[pp]);
+                }
+                if (has_t) {
+                    // u[e] = words 4 n4 .. of k row 4 qt + e, rotated: word j = word (j + rot) % 4
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (rot & 1u) u[e] = make_uint4(u[e].y, u[e].z, u[e].w, u[e].x);
+                        if (rot & 2u) u[e] = make_uint4(u[e].z, u[e].w, u[e].x, u[e].y);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        uint2 pl[4];
+                        limbs4(word_of(u[0], j), word_of(u[1], j), word_of(u[2], j), word_of(u[3], j), pl);
+                        const uint32_t off = sw64_off(4u * n4 + ((j + rot) & 3u), qt);
+#pragma unroll
+                        for (int pp = 0; pp < 4; ++pp) sts64(plane + 4u * kT2PlaneA + pp * S2::kPlaneB + off, pl[pp]);
+                    }
+                }
+                // The tensor core reads the planes, and the next copy into the raw stage writes,
+                // through the async proxy: one fence orders this thread's plane stores and raw
+                // reads before both.  (Releasing the raw stage before the conversion, with its own
+                // fence, measured slower; without that fence the copy overwrote words not yet read.)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(base + S2::kPlFull + 8u * pq);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(base + S2::kRawEmpty + 8u * r);  // one arrival per warp
+            }
+        };
+        if (rows_valid == kTcM)
+            convert_all(std::true_type{});
+        else
+            convert_all(std::false_type{});
     } else if (warp == kT2TmaWarp) {
         // ---- copies: raw stage g % 4 once every conversion warp released it ------
         if (lane == 0) {
