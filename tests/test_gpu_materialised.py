@@ -179,6 +179,7 @@ def _tc_contract(torch, pir, S, T, pad=0):
     (5, 1000, 16, 0),               # batch and width below one tile: copies mostly past the edges
     (1, 4, 4, 0),                   # k below one 32-value stage
     (3, 70, 8, 2),                  # ragged k stage, aligned rows
+    (150, 3000, 32, 0),             # 32-word tiles, the second query tile 22 rows deep
 ])
 def test_tc_contract_matches_oracle(env, tc_kernel, B, L, W, pad):
     torch, pir, orc = env
