@@ -576,6 +576,12 @@ int pir_server_eval_pbr(const pir_table* t, uint64_t bin_rows, const uint8_t* dk
     const uint64_t nbins = (t->rows + bin_rows - 1) / bin_rows;
     if (nbins > 0xffffffffull) return PIR_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    {
+        // one launch: each CTA expands its bins' trees, then multiplies its own rows
+        const int rc = launch_pbr_fused(t->data, t->rows, t->width, t->stride, bin_rows, n, dkeys, (uint32_t)nbins,
+                                        dout, dstatus, stream);
+        if (rc != PIR_ERR_UNSUPPORTED) return rc;
+    }
     if (scan_bins_supported(t->data, t->stride, t->width, bin_rows)) {
         // two passes: every bin's share vector into scratch (one word per table row,
         // nbins x bin_rows words from the staging pool), then one streaming pass over

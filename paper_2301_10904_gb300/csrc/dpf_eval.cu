@@ -1341,8 +1341,12 @@ __device__ __forceinline__ uint4 expand1(uint32_t lane4, uint32_t lane4h, const 
     return xor4(c, w);
 }
 
-__global__ void __launch_bounds__(kProducers, 1) expand_bfs_kernel(const BfsParams p) {
-    if (!smem_base_ok(p.status)) return;
+// The expansion of a BFS CTA's units.  KEEP: the leaf shares stay in shared
+// memory at yleaf[unit * 2^(n-u) + leaf] (unit-major), instead of going to
+// p.shares; the level above the leaf parents, where yleaf lies, is free by
+// then.  Ends with the leaf parents' loop (no barrier after it).
+template <bool KEEP>
+__device__ __forceinline__ void bfs_expand(const BfsParams& p, uint32_t* yleaf) {
     const int tid = threadIdx.x;
     const uint32_t lane4 = (uint32_t)(tid & 31) << 2, lane4h = lane4 | 128u;
     const uint32_t t0 = blockIdx.x * p.upc;
@@ -1420,6 +1424,12 @@ __global__ void __launch_bounds__(kProducers, 1) expand_bfs_kernel(const BfsPara
                 y1 = 0u - y1;
             }
         }
+        if constexpr (KEEP) {
+            const uint32_t l = (i & jmask) * 2u;
+            yleaf[(t << h) + l] = y0;
+            yleaf[(t << h) + l + 1u] = y1;
+            continue;
+        }
         uint32_t* dst = p.shares + (uint64_t)(g >> u) * p.ld + j;
         if (j + 1 < p.rows) {
             if (p.vec2)
@@ -1433,6 +1443,168 @@ __global__ void __launch_bounds__(kProducers, 1) expand_bfs_kernel(const BfsPara
         }
     }
 }
+
+__global__ void __launch_bounds__(kProducers, 1) expand_bfs_kernel(const BfsParams p) {
+    if (!smem_base_ok(p.status)) return;
+    bfs_expand<false>(p, nullptr);
+}
+
+// ------------------------------- partial batch retrieval: expansion, then rows
+// The breadth-first expansion above with the leaf shares kept in shared
+// memory, followed in the same CTA by the product with the table rows of its
+// own units (Sec. 4, batch PIR: a bin's rows meet only its own query).  A
+// unit's rows are one contiguous run of the dense table; the CTA brings them
+// in, in pieces of at most kPbrStageBytes, by bulk copies into a ring laid
+// over the lookup tables (no longer needed), multiplies each row by its
+// unit's leaf share, and adds its sums into the bin's output words when the
+// bin changes (a bin's units are consecutive).  No share vector reaches HBM
+// (Sec. 3.2.4).  Every wait is bounded; one that gives up sets
+// PIR_FAULT_WAIT_TIMEOUT and the CTA skips the rest of its products.  (The
+// two phases do not overlap: every CTA expands, then every CTA reads, so the
+// step costs the expansion plus one streaming pass over the table.  An L2
+// prefetch of each CTA's first rows during the expansion measured slower.)
+constexpr uint32_t kPbrStageBytes = 32 * 1024;
+constexpr uint32_t kPbrStages = (uint32_t)kTablesBytes / kPbrStageBytes;
+constexpr int kPbrBarOff = kBfsSmemBytes;  // kPbrStages full barriers
+constexpr int kPbrAbortOff = kPbrBarOff + 8 * (int)kPbrStages;
+constexpr int kPbrSmemBytes = kPbrAbortOff + 16;
+constexpr uint32_t kPbrSpinLimit = 1u << 22;
+static_assert(kPbrStages >= 2 && kPbrStages * kPbrStageBytes <= (uint32_t)kTablesBytes, "ring over the tables");
+static_assert(kPbrSmemBytes <= 232448, "dynamic shared memory above the 227 KiB a CTA may use");
+static_assert(kBfsOff == kTablesBytes && kBfsLastBytes >= 4 * 2048, "reduction buffer in the leaf parents' level");
+
+struct PbrParams {
+    BfsParams b;
+    const uint32_t* table;  // dense rows: row j at table + j * width
+    uint64_t table_rows;
+    uint64_t bin_rows;      // bin k: rows [k * bin_rows, k * bin_rows + bin_rows)
+    uint32_t width;         // words, a multiple of 4, at most 2048
+    uint32_t rpp;           // rows per piece (a piece is at most kPbrStageBytes)
+    uint32_t ppu;           // pieces per unit: ceil(2^(n-u) / rpp)
+    uint32_t* out;          // nbins x width words, accumulated into (zeroed by the caller)
+    uint32_t* faults;       // the library's device fault word
+};
+
+struct PbrPiece {
+    uint64_t row0;  // first table row
+    uint32_t rows;  // rows to copy and multiply (0 past the bin or the table)
+    uint32_t t;     // unit of the CTA
+    uint32_t leaf;  // unit-relative leaf of row0
+};
+
+// Piece k of the CTA whose first unit is t0.
+__device__ __forceinline__ PbrPiece pbr_piece(const PbrParams& p, uint32_t t0, uint32_t k) {
+    const uint32_t h = p.b.n - p.b.u;
+    const uint32_t t = k / p.ppu, pi = k - t * p.ppu;
+    const uint32_t g = t0 + t;
+    const uint64_t key = g >> p.b.u;
+    const uint32_t leaf = pi * p.rpp;
+    const uint64_t j0 = ((uint64_t)(g & ((1u << p.b.u) - 1u)) << h) + leaf;  // bin-relative row
+    uint64_t rows = min((uint64_t)p.rpp, (uint64_t)((1ull << h) - leaf));
+    rows = j0 < p.bin_rows ? min(rows, p.bin_rows - j0) : 0;
+    const uint64_t row0 = key * p.bin_rows + j0;
+    rows = row0 < p.table_rows ? min(rows, p.table_rows - row0) : 0;
+    return PbrPiece{row0, (uint32_t)rows, t, leaf};
+}
+
+__global__ void __launch_bounds__(kProducers, 1) pbr_bfs_scan_kernel(const PbrParams p) {
+    if (!smem_base_ok(p.b.status)) return;
+    const int tid = threadIdx.x;
+    const uint32_t t0 = blockIdx.x * p.b.upc;
+    const uint32_t nt = min(p.b.upc, p.b.nunits - t0);
+    const uint32_t npieces = nt * p.ppu;
+    const uint32_t h = p.b.n - p.b.u;
+    const uint32_t W = p.width;
+    const uint32_t bar0 = smem_addr(sm + kPbrBarOff);
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(sm + kPbrAbortOff);
+    if (tid == 0) {
+        for (uint32_t st = 0; st < kPbrStages; ++st) mbar_init(bar0 + 8u * st, 1u);
+        *abort_flag = 0u;
+        fence_mbarrier_init();
+    }
+    uint32_t* yleaf = reinterpret_cast<uint32_t*>(sm + kBfsOff + kBfsLastBytes);
+    bfs_expand<true>(p.b, yleaf);  // (its table set-up ends with a CTA barrier: the mbarriers are visible)
+
+    // ---- the CTA's rows: a ring of kPbrStages pieces over the lookup tables ----
+    fence_proxy_async_smem();  // the tables' generic accesses before the copies overwrite them
+    __syncthreads();           // ... and every leaf share is in yleaf
+    uint32_t issued = 0;  // pieces copies were started for (thread 0)
+    auto issue = [&](uint32_t k) {
+        issued = k + 1;
+        const PbrPiece pc = pbr_piece(p, t0, k);
+        const uint32_t st = k % kPbrStages, bytes = pc.rows * W * 4u;
+        mbar_expect_tx(bar0 + 8u * st, bytes);
+        if (bytes) bulk_g2s(smem_addr(sm + st * kPbrStageBytes), p.table + pc.row0 * W, bytes, bar0 + 8u * st);
+    };
+    if (tid == 0)
+        for (uint32_t k = 0; k < min(kPbrStages, npieces); ++k) issue(k);
+    const uint32_t nc = W / 4u, nrg = (uint32_t)kProducers / nc;
+    const uint32_t c = (uint32_t)tid % nc, rg = (uint32_t)tid / nc;
+    const bool active = rg < nrg;
+    uint32_t* red = reinterpret_cast<uint32_t*>(sm + kBfsOff);  // the leaf parents' level: free now
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    // this thread's sums into the bin's output words (every thread of the CTA)
+    auto flush = [&](uint64_t key) {
+        for (uint32_t i = (uint32_t)tid; i < W; i += kProducers) red[i] = 0u;
+        __syncthreads();
+        if (nc < 32 && (nc & (nc - 1)) == 0) {  // lanes lane, lane + nc, ... hold the same words
+            for (uint32_t off = 16; off >= nc; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+            if (((uint32_t)tid & 31u) < nc)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (acc[i]) atomicAdd(&red[c * 4u + i], acc[i]);
+        } else if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (acc[i]) atomicAdd(&red[c * 4u + i], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = 0u;
+        __syncthreads();
+        for (uint32_t i = (uint32_t)tid; i < W; i += kProducers)
+            if (red[i]) atomicAdd(p.out + key * W + i, red[i]);
+        __syncthreads();  // red is cleared again by the next flush
+    };
+    uint64_t cur = (uint64_t)t0 >> p.b.u;
+    for (uint32_t k = 0; k < npieces; ++k) {
+        const PbrPiece pc = pbr_piece(p, t0, k);
+        const uint64_t key = (uint64_t)(t0 + pc.t) >> p.b.u;
+        if (key != cur) {  // uniform: every thread walks the same pieces
+            flush(cur);
+            cur = key;
+        }
+        const uint32_t st = k % kPbrStages;
+        if (!*abort_flag && !mbar_wait_bounded(bar0 + 8u * st, (k / kPbrStages) & 1u, kPbrSpinLimit)) {
+            if (tid == 0) atomicOr(p.faults, PIR_FAULT_WAIT_TIMEOUT);
+            *abort_flag = 1u;
+        }
+        if (!*abort_flag && active && pc.rows) {
+            const char* stage = sm + st * kPbrStageBytes;
+            const uint32_t* ys = yleaf + (pc.t << h) + pc.leaf;
+            for (uint32_t rr = rg; rr < pc.rows; rr += nrg) {
+                const uint4 v = *reinterpret_cast<const uint4*>(stage + (rr * W + c * 4u) * 4u);
+                const uint32_t y = ys[rr];
+                acc[0] += y * v.x;
+                acc[1] += y * v.y;
+                acc[2] += y * v.z;
+                acc[3] += y * v.w;
+            }
+        }
+        fence_proxy_async_smem();  // these reads before the next copy into the stage
+        __syncthreads();
+        if (tid == 0 && !*abort_flag && k + kPbrStages < npieces) issue(k + kPbrStages);
+    }
+    flush(cur);
+    if (tid == 0 && *abort_flag) {
+        // copies still landing after a wait gave up: see the last one of each stage
+        // in (bounded; its phase is the stage's last, so a finished one reads as such)
+        for (uint32_t k = issued > kPbrStages ? issued - kPbrStages : 0u; k < issued; ++k)
+            mbar_wait_bounded(bar0 + 8u * (k % kPbrStages), (k / kPbrStages) & 1u, kPbrSpinLimit);
+    }
+}
+
 
 // Many tables of different sizes and widths in one launch.  Items are
 // (table, row range, up to 8 queries of that table); CTAs take the next item
@@ -1731,17 +1903,18 @@ static uint32_t grid_for(uint64_t items) {
 // (expand_bfs_kernel).  PIR_ERR_UNSUPPORTED where a CTA would hold more than
 // kBfsMaxUnits units or kBfsMaxLeaves leaves for every u, or the rows do not
 // start at the domain's first leaf.
-static int launch_expand_bfs(const EvalRequest& req, uint32_t* shares, uint64_t ld, cudaStream_t s) {
-    if (req.row_lo != 0 || req.batch == 0 || req.n == 0 || req.n > 31) return PIR_ERR_UNSUPPORTED;
+// The breadth-first kernels' cut of `batch` trees of n levels: unit depth u
+// with the fewest leaves on the busiest CTA (ties: the smaller u, fewer path
+// walks), within the CTA's level buffers and header slots.  False when no u fits.
+static bool bfs_cut(uint32_t batch, uint32_t n, int* u_out, uint64_t* upc_out) {
+    if (batch == 0 || n == 0 || n > 31) return false;
     const uint64_t sms = (uint64_t)std::max(1, device_sm_count());
-    // unit depth u: the fewest leaves on the busiest CTA (ties: the smaller u,
-    // fewer path walks), within the CTA's level buffers and header slots
     int best_u = -1;
     uint64_t best_upc = 0, best_load = ~0ull;
-    for (int u = 0; u <= std::min(3, (int)req.n - 1); ++u) {
-        const uint64_t units = (uint64_t)req.batch << u;
+    for (int u = 0; u <= std::min(3, (int)n - 1); ++u) {
+        const uint64_t units = (uint64_t)batch << u;
         const uint64_t upc = (units + std::min(units, sms) - 1) / std::min(units, sms);
-        const uint64_t load = upc << (req.n - u);  // leaves of the busiest CTA
+        const uint64_t load = upc << (n - u);  // leaves of the busiest CTA
         if (upc > dev::kBfsMaxUnits || load > dev::kBfsMaxLeaves || units > 0xffffffffull) continue;
         if (load < best_load) {
             best_load = load;
@@ -1749,7 +1922,16 @@ static int launch_expand_bfs(const EvalRequest& req, uint32_t* shares, uint64_t 
             best_upc = upc;
         }
     }
-    if (best_u < 0) return PIR_ERR_UNSUPPORTED;
+    *u_out = best_u;
+    *upc_out = best_upc;
+    return best_u >= 0;
+}
+
+static int launch_expand_bfs(const EvalRequest& req, uint32_t* shares, uint64_t ld, cudaStream_t s) {
+    if (req.row_lo != 0) return PIR_ERR_UNSUPPORTED;
+    int best_u = -1;
+    uint64_t best_upc = 0;
+    if (!bfs_cut(req.batch, req.n, &best_u, &best_upc)) return PIR_ERR_UNSUPPORTED;
     dev::BfsParams p{};
     p.keys = req.dkeys;
     p.key_bytes = (uint32_t)key_bytes(req.n);
@@ -1771,6 +1953,53 @@ static int launch_expand_bfs(const EvalRequest& req, uint32_t* shares, uint64_t 
         e = dev::smem_attribute_once(dev::expand_bfs_kernel, dev::kBfsSmemBytes, true);  // after a reset
     }
     return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "expand_bfs launch");
+}
+
+// Partial batch retrieval in one launch (pbr_bfs_scan_kernel).  Clears dout
+// first.  PIR_ERR_UNSUPPORTED unless the table is dense (stride == width), its
+// rows 16-byte multiples of at most 2048 words, and the bins' trees fit the
+// breadth-first cut.
+int launch_pbr_fused(const uint32_t* table, uint64_t rows, uint32_t width, uint64_t stride, uint64_t bin_rows,
+                     uint32_t n, const uint8_t* dkeys, uint32_t nbins, uint32_t* dout, uint32_t* dstatus,
+                     void* stream) {
+    if (!reserved_smem_ok()) return PIR_ERR_UNSUPPORTED;
+    if (stride != width || width % 4 != 0 || width > 2048 || (reinterpret_cast<uintptr_t>(table) & 15u) != 0)
+        return PIR_ERR_UNSUPPORTED;
+    int u = -1;
+    uint64_t upc = 0;
+    if (!bfs_cut(nbins, n, &u, &upc)) return PIR_ERR_UNSUPPORTED;
+    uint32_t* faults = device_fault_word();
+    if (!faults) return cuda_fail((int)cudaGetLastError(), "device fault word");
+    dev::PbrParams p{};
+    p.b.keys = dkeys;
+    p.b.key_bytes = (uint32_t)key_bytes(n);
+    p.b.n = n;
+    p.b.u = (uint32_t)u;
+    p.b.nunits = nbins << u;
+    p.b.upc = (uint32_t)upc;
+    p.b.rows = bin_rows;
+    p.b.status = dstatus;
+    const uint32_t h = n - (uint32_t)u;
+    p.table = table;
+    p.table_rows = rows;
+    p.bin_rows = bin_rows;
+    p.width = width;
+    p.rpp = (uint32_t)std::min<uint64_t>(std::max<uint32_t>(1u, dev::kPbrStageBytes / (width * 4u)), 1ull << h);
+    p.ppu = (uint32_t)(((1ull << h) + p.rpp - 1) / p.rpp);
+    p.out = dout;
+    p.faults = faults;
+    const uint32_t ctas = (uint32_t)((p.b.nunits + upc - 1) / upc);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(dout, 0, (uint64_t)nbins * width * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "memset shares");
+    e = dev::smem_attribute_once(dev::pbr_bfs_scan_kernel, dev::kPbrSmemBytes);
+    for (int attempt = 0; e == cudaSuccess && attempt < 2; ++attempt) {
+        dev::pbr_bfs_scan_kernel<<<ctas, dev::kProducers, dev::kPbrSmemBytes, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaErrorInvalidValue || attempt > 0) break;
+        e = dev::smem_attribute_once(dev::pbr_bfs_scan_kernel, dev::kPbrSmemBytes, true);  // after a reset
+    }
+    return e == cudaSuccess ? PIR_OK : cuda_fail((int)e, "pbr_bfs_scan launch");
 }
 
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream) {

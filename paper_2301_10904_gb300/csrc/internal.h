@@ -114,6 +114,11 @@ int launch_fused(const EvalRequest& req, const pir_plan& plan, void* stream);
 int plan_bins(uint64_t bin_rows, uint32_t n, uint32_t width, uint32_t nbins, pir_plan* plan);
 int launch_bins(const EvalRequest& req, uint64_t bin_rows, const pir_plan& plan, void* stream);
 int launch_materialise(const EvalRequest& req, const pir_plan& plan, uint32_t* shares, uint64_t ld, void* stream);
+// partial batch retrieval in one launch: the bins' trees breadth first, then each
+// CTA's own rows of a dense table (clears dout); PIR_ERR_UNSUPPORTED outside its layouts
+int launch_pbr_fused(const uint32_t* table, uint64_t rows, uint32_t width, uint64_t stride, uint64_t bin_rows,
+                     uint32_t n, const uint8_t* dkeys, uint32_t nbins, uint32_t* dout, uint32_t* dstatus,
+                     void* stream);
 
 // share matrix x table mod 2^32 (contract.cu); out is accumulated into
 int launch_contract(const uint32_t* shares, uint64_t ld, uint32_t batch, const uint32_t* table, uint64_t stride,
