@@ -147,3 +147,35 @@ def test_pbr_full_size(env):
     for b in (0, 511, nbins - 1):
         T = table[b * bin_rows:(b + 1) * bin_rows].cpu().numpy().view(np.uint32)
         assert np.array_equal(outs[0][b], orc.answer(k0[b * kb:(b + 1) * kb], T))
+
+
+@pytest.mark.parametrize("rows,bin_rows,W", [(1 << 16, 1 << 10, 64), (5000, 1000, 16), (3000, 2, 4)])
+def test_pbr_one_launch_equals_the_two_launch_forms(env, rows, bin_rows, W):
+    """A dense table takes the one-launch kernel (trees breadth first, then each
+    CTA's own rows); the same rows at a padded stride take the expand-and-scan
+    or the bins kernel.  Both give the oracle's shares word for word, with a
+    bad key among the bins (zero share, status bit), and the status words agree."""
+    torch, pir, orc = env
+    T = wl.table_u32(rows + bin_rows + W, rows, W)
+    rng = np.random.Generator(np.random.PCG64(rows + W))
+    wanted = rng.integers(0, rows, max(1, rows // bin_rows)).tolist()
+    ks0, _, _, _, _ = _oracle_keys(orc, rows, bin_rows, wanted, rows + 3)
+    bad = bytearray(ks0[1])
+    bad[0] ^= 0xFF  # magic
+    ks0[1] = bytes(bad)
+    dense = dev_table(torch, T)
+    padded_full = torch.zeros((rows, W + 4), dtype=torch.int32, device="cuda")
+    padded_full[:, :W] = dense
+    padded = padded_full[:, :W]
+    outs, stats = [], []
+    for table in (dense, padded):
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        outs.append(_run(torch, pir, table, bin_rows, ks0, W, status))
+        stats.append(int(status.item()))
+    assert np.array_equal(outs[0], outs[1])
+    assert stats[0] == stats[1] and stats[0] & pir.PIR_STATUS_BAD_KEY
+    assert not outs[0][1].any()
+    nbins = len(ks0)
+    for b in sorted({0, nbins - 1, *rng.integers(0, nbins, 6).tolist()} - {1}):
+        lo = b * bin_rows
+        assert np.array_equal(outs[0][b], orc.answer(ks0[b], T[lo:lo + bin_rows])), b
